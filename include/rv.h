@@ -1,0 +1,189 @@
+/*
+ * rv.h -- C ABI of librv, B300-native runtime verification of LTL4-C formulas.
+ *
+ * LTL4-C ("Accelerated Runtime Verification of LTL Specifications with
+ * Counting Semantics", Medhat, Joshi, Bonakdarpour, Fischmeister) is LTL with
+ * four-valued runtime semantics (Def. "LTL4 semantics", Sec. 2.2.2) under a
+ * string of counting quantifiers: A (percentage of instances) and E (number
+ * of instances), each with a numeric constraint (Def. 1, Sec. 2.1).  A trace
+ * verdict is one of six truth values (Sec. 2.3, Def. "LTL4-C Semantics").
+ *
+ * The library implements Algorithm 1 (Sec. 4.2) on one GPU:
+ *   map      (SortTrace)          events grouped by binding key,
+ *   monitor  (Distribute)         each binding's LTL4 Moore monitor steps over
+ *                                 its projected sub-trace,
+ *   reduce   (ApplyQuantifiers)   per-parent verdict counts, then each
+ *                                 quantifier's constraint in exact integers.
+ *
+ * Conventions for every entry point:
+ *   - Return an rv_status; RV_OK (0) means success.  rv_last_error() gives a
+ *     thread-local message for the last failure.  No C++ exception and no
+ *     process exit crosses this interface; device-side faults are reported
+ *     through a device status word, never by trapping.
+ *   - The caller owns every input and output buffer.  The library owns the
+ *     objects it returns (rv_formula, rv_service, rv_stream) and frees them in
+ *     the matching *_free / *_close call.
+ *   - "device pointer" means memory of the current CUDA device; "host
+ *     pointer" means ordinary (or pinned) host memory.
+ *   - Timestamps are optional everywhere: the order of a trace is its array
+ *     order (Sec. 2, Def. "Trace"); when a ts array is given it is checked to
+ *     be non-decreasing and a violation returns RV_EINVAL.
+ */
+#ifndef RV_H
+#define RV_H
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  RV_OK = 0,
+  RV_EPARSE = 1,        /* formula text does not follow Def. 1 */
+  RV_EUNSUPPORTED = 2,  /* more than 16 monitor states, > 2 quantifiers, too large a body */
+  RV_EINVAL = 3,        /* bad argument or bad trace (predicate code out of range, ts decreasing) */
+  RV_ENOMEM = 4,        /* workspace too small or allocation failed */
+  RV_EAGAIN = 5,        /* streaming: chunk not admitted now (memory budget), retry later */
+  RV_ETIMEOUT = 6,      /* poll timed out, or a bounded device wait gave up */
+  RV_ECUDA = 7,         /* a CUDA runtime call failed */
+  RV_EINTERNAL = 8      /* device status word reports an internal limit/bug */
+} rv_status;
+
+/* Six truth values in their lattice order F < Fc < Fp < Tp < Tc < T (Sec. 2.3). */
+typedef enum {
+  RV_BOT = 0, RV_BOT_C = 1, RV_BOT_P = 2, RV_TOP_P = 3, RV_TOP_C = 4, RV_TOP = 5
+} rv_verdict;
+
+enum { RV_ONEHOT = 0, RV_BITMASK = 1 };          /* alphabet modes */
+enum { RV_Q_A = 0, RV_Q_E = 1 };                 /* quantifier kinds (Eq. bigq) */
+enum { RV_LT = 0, RV_LE = 1, RV_GT = 2, RV_GE = 3, RV_EQ = 4 };  /* comparison ~ */
+
+#define RV_MAX_STATES 16
+#define RV_MAX_LETTERS 256
+
+/* Interpretation of the predicate byte of an event (Sec. 2: events are sets
+ * of predicates).  RV_ONEHOT: code c is the single predicate code_names[c]
+ * (n_codes <= 256).  RV_BITMASK: bit i of the byte means code_names[i] holds
+ * (n_codes <= 8), so one event can carry several predicates.
+ * key_bits: width of the key column, 32 or 64.  With two quantified variables
+ * the key must be 64-bit and holds (d0 << 32) | d1. */
+typedef struct {
+  int n_codes;
+  const char* const* code_names;
+  int alphabet;
+  int key_bits;
+} rv_schema;
+
+typedef struct rv_formula rv_formula;
+
+typedef struct {
+  int n_quant;     /* 0, 1 or 2 counting quantifiers */
+  int n_states;    /* states of the minimal LTL4 Moore monitor of the body (<= 16) */
+  int n_letters;   /* number of distinct predicate bytes: n_codes or 2^n_codes */
+  int q0;          /* initial monitor state */
+  int key_bits;
+  int alphabet;
+} rv_formula_info;
+
+/* Parse `text` (Def. 1 syntax, defaults A = A_{=1}, E = E_{>=1}; see the
+ * DESIGN notes for the concrete grammar) and synthesise the LTL4 monitor of
+ * its body over the schema's alphabet (Def. "LTL4 Monitor", Sec. 2.2.3).
+ * On error returns RV_EPARSE / RV_EUNSUPPORTED / RV_EINVAL and writes a
+ * message into err[errlen] (may be NULL).  *out is owned by the caller and
+ * released with rv_formula_free.  Host only; no GPU work. */
+rv_status rv_compile_formula(const char* text, const rv_schema* schema, rv_formula** out,
+                             char* err, size_t errlen);
+rv_status rv_formula_get_info(const rv_formula* f, rv_formula_info* info);
+/* Monitor tables (host copies): maps[l] for each letter l < n_letters holds the
+ * transition map of letter l with nibble s = delta(s, l); labels[s] is the
+ * verdict lambda(s) in rv_verdict coding (one of F, Fp, Tp, T). */
+rv_status rv_formula_tables(const rv_formula* f, uint64_t* maps, int n_maps, uint8_t labels[16]);
+/* Quantifier tuple <Q_i, ~_i, c_i> of level i (Eq. bigq): kind RV_Q_A/E,
+ * op RV_LT..RV_EQ, constant num/den (den = 1 for E). */
+rv_status rv_formula_quantifier(const rv_formula* f, int level, int* kind, int* op,
+                                uint64_t* num, uint64_t* den);
+void rv_formula_free(rv_formula* f);
+
+/* Six-valued valuation of one quantifier node from its child-verdict counts
+ * v[0..5] (Eq. S and Def. "LTL4-C Semantics"; readings in the DESIGN notes).
+ * Host entry of the same function the reduce kernels run. */
+rv_status rv_valuate(int kind, int op, uint64_t num, uint64_t den, const uint64_t v[6], int* verdict);
+
+/* ------------------------------------------------------------------ offline verification */
+
+/* A trace as a structure of arrays in trace order: key (uint32 or uint64 per
+ * key_bits), pred (uint8 predicate byte), optional ts (uint32, may be NULL). */
+typedef struct {
+  const void* key;
+  const uint8_t* pred;
+  const uint32_t* ts;
+  uint64_t n;
+} rv_trace;
+
+typedef struct {
+  int32_t root;               /* [u |=_6 phi] as rv_verdict */
+  int32_t status;             /* rv_status of the device work */
+  uint64_t root_counts[6];    /* the root's child-verdict vector v (Sec. 3.4) */
+  uint64_t level_counts[2][6];/* verdict histogram of the level-1 and level-2 nodes */
+  uint64_t n_nodes[2];        /* number of distinct D|^1 and D|^2 (value-vector prefixes) */
+  uint64_t events;
+} rv_result;
+
+/* Optional per-binding outputs (device pointers, caller-owned).  keys/verdicts
+ * receive one entry per innermost binding (LTL4 verdict); outer_* one entry per
+ * level-1 node of a two-quantifier formula (six-valued verdict).  The order is
+ * unspecified.  Capacity n (events) always suffices. */
+typedef struct {
+  uint64_t* keys;
+  uint8_t* verdicts;
+  uint64_t capacity;
+  uint64_t* outer_keys;
+  uint8_t* outer_verdicts;
+  uint64_t outer_capacity;
+} rv_bindings;
+
+/* Tuning knobs; zero means "choose automatically". */
+typedef struct {
+  int bucket_bits;       /* log2 of the first-level key buckets, 8..11 */
+  int sub_bucket_bits;   /* log2 of the second-level split, 0..6 */
+  int unit_records;      /* records folded by one CTA, multiple of 256 */
+} rv_verify_opts;
+
+/* Device memory the offline path needs for a trace of n events
+ * (host_input != 0 adds room to stage host arrays on the device). */
+size_t rv_verify_workspace_size(const rv_formula* f, uint64_t n, int host_input,
+                                const rv_verify_opts* opts);
+
+/* Verify one trace against one formula (Algorithm 1: SortTrace, SpawnMonitors,
+ * Distribute, ApplyQuantifiers).  on_device != 0: t's arrays are device
+ * pointers; otherwise host pointers that are copied in on stream s.  ws is a
+ * device workspace of at least rv_verify_workspace_size bytes (NULL: the
+ * library allocates and frees one).  Blocks until the result is in *out.
+ * Errors: RV_EINVAL (bad trace), RV_ENOMEM (workspace), RV_ECUDA. */
+rv_status rv_verify_trace(const rv_formula* f, const rv_trace* t, int on_device, void* ws,
+                          size_t ws_bytes, rv_result* out, const rv_bindings* bindings,
+                          const rv_verify_opts* opts, cudaStream_t s);
+
+/* Asynchronous form for device-resident traces: enqueues all work on s and
+ * writes the result into the device struct *dev_out; no host synchronisation.
+ * The caller reads dev_out after synchronising s. */
+rv_status rv_verify_trace_async(const rv_formula* f, const rv_trace* t, void* ws, size_t ws_bytes,
+                                rv_result* dev_out, const rv_bindings* bindings,
+                                const rv_verify_opts* opts, cudaStream_t s);
+
+/* Last error message of the calling thread (never NULL). */
+const char* rv_last_error(void);
+
+/* Device allocator used when the library needs device memory of its own
+ * (ws == NULL, streaming service).  NULL restores cudaMalloc/cudaFree. */
+typedef void* (*rv_alloc_fn)(size_t bytes, void* ctx);
+typedef void (*rv_free_fn)(void* ptr, void* ctx);
+void rv_set_allocator(rv_alloc_fn alloc, rv_free_fn free_fn, void* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RV_H */
