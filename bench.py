@@ -1,0 +1,315 @@
+"""Throughput benchmark: verified events/s of map -> monitor -> reduce on B300.
+
+    python bench.py [--gpus N --steps K --warmup W] [--workload c2|c1|c3]
+    python bench.py --impl reference ...      # the CPU oracle on the same workload
+
+A step is one rv_verify_trace of the whole synthetic trace (all stages: key
+multisplit, monitor fold, combine, quantifier reduce) with the trace already
+resident in HBM.  The trace (0.5 GB for the default workload) is larger than
+L2, so no flush is needed between steps.  ``e2e`` repeats the measurement
+through the same C ABI with pinned HOST buffers: the host->device copy of the
+events and the device->host copy of the verdict are inside its timed region.
+Under torchrun every rank verifies its own trace of the same shape (weak
+scaling; no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # single formula over a socket trace, Zipf(1.1) cluster sizes, 1e8 events
+    "c2": dict(formula="A_{>=0.95} s: socket(s) => G(receive -> F respond)", kind="socket", n=100_000_000,
+               n_ids=1_000_000, zipf=1.1, pending_frac=0.03, key_bits=32, cfg=2),
+    "c1": dict(formula="A_{>=0.95} s: socket(s) => G(receive -> F respond)", kind="socket", n=100_000,
+               n_ids=1000, zipf=None, n_pending=50, key_bits=32, cfg=1),
+    "c3": dict(formula="A_{>=0.90} u: user(u) => E_{<=3} f: file(u,f) => open && !F close", kind="file",
+               n=200_000_000, n_users=100_000, n_files=1_000_000, key_bits=64, cfg=3),
+}
+# algorithmic bytes per event: one read of the key and of the predicate byte
+ALG_BYTES = {"c1": 5, "c2": 5, "c3": 9}
+
+
+def make_trace(w, seed):
+    from paper_1411_2239_b300 import synth
+    if w["kind"] == "socket":
+        return synth.socket_trace(w["n"], w["n_ids"], pending_frac=w.get("pending_frac"),
+                                  n_pending=w.get("n_pending"), zipf_s=w["zipf"], seed=seed)
+    return synth.file_trace(w["n"], w["n_users"], w["n_files"], seed=seed)
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except Exception:
+        return {"hbm_gbs": 6400.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu, self.p, self.path = gpu, None, f"/tmp/rv_clocks_{os.getpid()}.csv"
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        time.sleep(0.3)
+        self.p.terminate()
+        self.p.wait()
+        self.f.close()
+        rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for nm, val in zip(names, r[5:9]):
+                    if val.strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(os.path.join(ROOT, "paper_1411_2239_b300", "csrc"))):
+        h.update(open(os.path.join(ROOT, "paper_1411_2239_b300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(kernel, workload):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was captured on the current kernel sources."""
+    try:
+        t = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+        e = t.get(f"{workload}:{kernel}")
+        if e and e.get("source_hash") == kernel_source_hash():
+            return e["dram_bytes_per_launch"]
+    except Exception:
+        pass
+    return None
+
+
+def cpu_baseline(w, trace, budget_s=20.0):
+    """The oracle, as it stands, on a bounded prefix of the same trace."""
+    from oracle.verify import Schema, verify
+    n = 20_000
+    sch = Schema(trace.codes)
+    while True:
+        t0 = time.perf_counter()
+        verify(w["formula"], sch, trace.key[:n], trace.pred[:n])
+        dt = time.perf_counter() - t0
+        if dt > budget_s / 4 or n >= trace.n:
+            break
+        n = min(trace.n, int(n * max(2.0, budget_s / 4 / max(dt, 1e-3))))
+    return {"value": n / dt, "unit": "events/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {n} events of the same trace, oracle.verify once ({dt:.1f} s)"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = WORKLOADS[args.workload]
+    trace = make_trace(w, 1000 * w["cfg"] + 0)
+    from oracle.verify import Schema, verify
+    n = min(trace.n, 200_000)
+    sch = Schema(trace.codes)
+    for _ in range(args.warmup):
+        verify(w["formula"], sch, trace.key[:n], trace.pred[:n])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        verify(w["formula"], sch, trace.key[:n], trace.pred[:n])
+    dt = (time.perf_counter() - t0) / args.steps
+    value = n / dt
+    line = {"metric": "verified events/s", "value": value, "unit": "events/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": workload_name(args.workload), "events_per_step": n},
+            "cpu_baseline": {"value": value, "unit": "events/s", "cores": 1, "kind": "oracle",
+                             "sample": f"first {n} events of the {args.workload} trace per step"},
+            "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def workload_name(k):
+    w = WORKLOADS[k]
+    if w["kind"] == "socket":
+        z = f", Zipf({w['zipf']})" if w["zipf"] else ", uniform"
+        return f"{w['formula']} over {w['n']:.0e} events, {w['n_ids']:.0e} socket ids{z}"
+    return f"{w['formula']} over {w['n']:.0e} events, {w['n_users']:.0e} users x {w['n_files']:.0e} files"
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2", choices=list(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+    from paper_1411_2239_b300 import rv
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+
+    w = WORKLOADS[args.workload]
+    trace = make_trace(w, 1000 * w["cfg"] + rank)
+    f = rv.Formula(w["formula"], trace.codes, key_bits=w["key_bits"])
+    kt = np.uint64 if w["key_bits"] == 64 else np.uint32
+    key_np = np.ascontiguousarray(trace.key.astype(kt))
+    key = torch.from_numpy(key_np.view(np.int64 if kt == np.uint64 else np.int32)).cuda()
+    pred = torch.from_numpy(trace.pred).cuda()
+    n = trace.n
+    stream = torch.cuda.current_stream()
+    ws = rv.workspace(rv.workspace_size(f, n))
+    dres = torch.empty(rv.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+
+    # correctness of this run: the construction's pending sockets are exactly the Fp children
+    first = rv.verify(f, key, pred)
+    verified = first.status == 0
+    if w["kind"] == "socket":
+        exp_fp = len(trace.meta["pending_ids"])
+        verified &= first.root_counts == [0, 0, exp_fp, trace.meta["appearing"] - exp_fp, 0, 0]
+
+    for _ in range(args.warmup):
+        rv.verify_async(f, key, pred, ws, dres)
+    torch.cuda.synchronize()
+    clk = Clocks(local)
+    clk.start()
+    time.sleep(0.4)
+    launches0 = rv.lib().rv_launch_count()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        rv.verify_async(f, key, pred, ws, dres)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    launches = rv.lib().rv_launch_count() - launches0
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    last = rv.parse_result(bytes(dres.cpu().numpy()))
+    verified &= last.root == first.root and last.root_counts == first.root_counts
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        v = torch.tensor([1 if verified else 0], device="cuda")
+        dist.all_reduce(v, op=dist.ReduceOp.MIN)
+        verified = bool(v.item())
+    value = n * world / (ms / 1e3)
+
+    # per-kernel durations (CUDA events on the launch stream) over a second timed pass
+    rv.lib().rv_profile_enable(1)
+    for _ in range(args.steps):
+        rv.verify_async(f, key, pred, ws, dres)
+    torch.cuda.synchronize()
+    rv.lib().rv_profile_enable(0)
+    stats = (StatArr * 64)()
+    nk = rv.lib().rv_profile_collect(stats, 64)
+    kern = {stats[i].name.decode(): (stats[i].launches, stats[i].total_ms) for i in range(nk)}
+    prof_total = sum(v[1] for v in kern.values())
+    top = max(kern, key=lambda k: kern[k][1])
+    top_launches, top_ms = kern[top]
+    avg_ms = top_ms / top_launches
+    pk, src = peaks()
+    achieved = ALG_BYTES[args.workload] * n / (avg_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / pk["hbm_gbs"], "traffic": traffic_for(top, args.workload),
+                "kernel": top, "kernel_share": top_ms / prof_total, "peak_source": f"{src} copy bandwidth",
+                "path_achieved": ALG_BYTES[args.workload] * n / (ms / 1e3) / 1e9,
+                "path_frac": ALG_BYTES[args.workload] * n / (ms / 1e3) / 1e9 / pk["hbm_gbs"]}
+    kernels = {k: {"launches": v[0], "avg_us": 1e3 * v[1] / v[0], "share": v[1] / prof_total} for k, v in kern.items()}
+
+    e2e = None
+    if not args.no_e2e:
+        kp = torch.empty(key.shape, dtype=key.dtype, pin_memory=True)
+        pp = torch.empty(pred.shape, dtype=pred.dtype, pin_memory=True)
+        kp.copy_(key.cpu())
+        pp.copy_(pred.cpu())
+        hk = kp.numpy().view(kt)
+        hp = pp.numpy()
+        ksteps = max(1, min(args.steps, 5))
+        rv.verify(f, hk, hp)   # warm
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(ksteps):
+            r = rv.verify(f, hk, hp)
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / ksteps
+        verified &= r.root == first.root and r.root_counts == first.root_counts
+        e2e = {"value": n / dt, "unit": "events/s", "h2d_bytes_per_step": int(hk.nbytes + hp.nbytes),
+               "d2h_bytes_per_step": rv.RESULT_BYTES, "steps": ksteps}
+
+    if rank != 0:
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w, trace)
+    line = {"metric": "verified events/s", "value": value if verified else 0.0, "unit": "events/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int",
+            "data": "synthetic (seeded; stands in for the paper's Apache/strace case study)",
+            "verified": verified,
+            "config": {"workload": workload_name(args.workload), "events": n, "bindings": int(first.n_nodes[0]),
+                       "root_verdict": rv.VERDICT_NAMES[first.root], "l2": "inputs larger than L2 (no flush)",
+                       "parallelism": f"weak x{world} (one independent trace per GPU)"},
+            "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": int(launches), "clocks": clocks}
+    print(json.dumps(line))
+
+
+class StatArr(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_uint64), ("total_ms", ctypes.c_double)]
+
+
+if __name__ == "__main__":
+    main()

@@ -174,6 +174,23 @@ rv_status rv_verify_trace_async(const rv_formula* f, const rv_trace* t, void* ws
                                 rv_result* dev_out, const rv_bindings* bindings,
                                 const rv_verify_opts* opts, cudaStream_t s);
 
+/* ------------------------------------------------------------------ instrumentation
+ * The paper times whole monitor runs (Sec. 5.2); these calls time each kernel.
+ * rv_profile_enable(1): every kernel launch of the library is bracketed by a
+ * pair of CUDA events recorded on the launching stream.  rv_profile_collect
+ * waits for the recorded events, adds their durations into per-kernel totals
+ * and copies up to max entries into out; it returns the number of distinct
+ * kernels and clears the totals.  rv_launch_count: kernels launched by the
+ * library in this process (profiling on or off). */
+typedef struct {
+  char name[48];
+  uint64_t launches;
+  double total_ms;
+} rv_kernel_stat;
+void rv_profile_enable(int on);
+int rv_profile_collect(rv_kernel_stat* out, int max);
+uint64_t rv_launch_count(void);
+
 /* Last error message of the calling thread (never NULL). */
 const char* rv_last_error(void);
 

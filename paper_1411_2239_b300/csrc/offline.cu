@@ -1,0 +1,1102 @@
+// Offline verification of one trace against one LTL4-C formula on one GPU
+// (Algorithm 1, Sec. 4.2: SortTrace -> SpawnMonitors -> Distribute ->
+// ApplyQuantifiers), re-designed for B300.
+//
+// map      k_hist / k_colscan_* / k_bucket_scan / k_scatter: a stable
+//          multisplit of the events into 2^B1 buckets by the top bits of the
+//          mixed outer key (optionally a second split k_hist2 / k_scan2 /
+//          k_scatter2 into 2^B2 sub-buckets).  Each warp owns a contiguous
+//          super-tile of the trace and private bucket cursors, so records keep
+//          trace order inside every bucket; a record is the letter plus the
+//          key bits the bucket does not imply (4 or 8 bytes).
+// monitor  k_fold: one CTA folds a unit (<= unit_records records of a bucket).
+//          Warps take contiguous slices of the unit; each key (binding) gets a
+//          slot in a shared-memory hash table and every warp composes the
+//          64-bit transition maps of its slice's letters per slot (equal keys
+//          inside a 32-record round are grouped with __match_any_sync and
+//          applied in lane order).  The warps' maps are then composed in
+//          order.  This is the per-cluster monitor of ProcessBuffer, with
+//          the long clusters of a Zipf head split across warps and CTAs and
+//          rejoined by associativity of map composition.
+// reduce   a bucket held by one unit is finalised in k_fold; buckets split
+//          over several units pass (key, map) pairs to k_combine, which
+//          composes them level by level in unit order (fan-in 16) and
+//          finalises at the last level.  Finalising evaluates lambda(map[q0]),
+//          counts verdicts per parent (per outer binding in a shared table
+//          for two quantifiers, all bindings of an outer value share its
+//          bucket), applies the quantifier constraint in integers, and adds
+//          the counts of the root.  k_root valuates the root.
+#include <cstdio>
+#include <cstring>
+#include <algorithm>
+#include <vector>
+
+#include "profile.h"
+#include "rv_device.cuh"
+
+using namespace rvd;
+
+namespace {
+
+constexpr int SC_WARPS = 8;
+constexpr int FOLD_WARPS = 8;
+constexpr int FOLD_THREADS = FOLD_WARPS * 32;
+constexpr int SLOTS = 1024;
+constexpr int HT_BITS = 11;
+constexpr int HT_CAP = 1 << HT_BITS;
+constexpr int UCAP = 256;
+constexpr int GC = 16;
+constexpr int TILE2 = 8192;
+constexpr int COLCHUNK = 64;
+constexpr uint16_t NO_SLOT = 0xFFFF;
+constexpr uint16_t FULL_SLOT = 0xFFFE;
+constexpr uint64_t EMPTY_KEY = ~0ull;
+constexpr unsigned FULL = 0xFFFFFFFFu;
+constexpr int SPIN_LIMIT = 1 << 22;
+
+struct Tile { uint32_t bucket, k, K, pad; uint64_t begin, end; };
+struct Item { uint64_t off; uint32_t cnt, pad; };
+struct Group { uint32_t bucket, first, cnt, k, K, pad; };
+struct Pair { uint64_t key, map; };
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+template <int F>
+__device__ __forceinline__ uint64_t load_key(const void* p, uint64_t i) {
+  if (F == FMT_K32) return ((const uint32_t*)p)[i];
+  return ((const uint64_t*)p)[i];
+}
+
+// ------------------------------------------------------------------ level-1 multisplit
+template <int F>
+__global__ void __launch_bounds__(SC_WARPS * 32)
+k_hist(const void* keyp, const uint32_t* ts, uint64_t n, uint64_t per_warp, int G_w, int B1, int nq,
+       uint32_t* hist, Acc* acc) {
+  extern __shared__ uint32_t sm_cnt[];
+  const int P = 1 << B1;
+  const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * SC_WARPS + wl;
+  uint32_t* cnt = sm_cnt + wl * P;
+  for (int b = lane; b < P; b += 32) cnt[b] = 0;
+  __syncwarp();
+  if (gw >= G_w) return;
+  const uint64_t begin = (uint64_t)gw * per_warp, end = min(n, begin + per_warp);
+  bool bad_ts = false;
+  for (uint64_t base = begin; base < end; base += 32) {
+    const uint64_t i = base + lane;
+    const bool v = i < end;
+    uint32_t b = 0xFFFFFFFFu;
+    if (v) {
+      b = make_record<F>(load_key<F>(keyp, i), 0, B1, nq).bucket;
+      if (ts && i > 0 && ts[i] < ts[i - 1]) bad_ts = true;
+    }
+    const uint32_t peers = __match_any_sync(FULL, b);
+    if (v && lane == __ffs(peers) - 1) cnt[b] += __popc(peers);
+    __syncwarp();
+  }
+  if (__any_sync(FULL, bad_ts) && lane == 0) atomicOr(&acc->err, ERR_TS);
+  for (int b = lane; b < P; b += 32) hist[(uint64_t)gw * P + b] = cnt[b];
+}
+
+// per (bucket, chunk of warps): chunk sums
+__global__ void k_colscan_a(const uint32_t* hist, int G_w, int P, int nchunk, uint64_t* part) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= P * nchunk) return;
+  const int b = t % P, c = t / P;
+  const int w0 = c * COLCHUNK, w1 = min(G_w, w0 + COLCHUNK);
+  uint64_t s = 0;
+  for (int w = w0; w < w1; ++w) s += hist[(uint64_t)w * P + b];
+  part[(uint64_t)c * P + b] = s;
+}
+// per bucket: exclusive scan over chunks, bucket totals
+__global__ void k_colscan_b(uint64_t* part, int P, int nchunk, uint64_t* tot) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= P) return;
+  uint64_t run = 0;
+  for (int c = 0; c < nchunk; ++c) {
+    uint64_t x = part[(uint64_t)c * P + b];
+    part[(uint64_t)c * P + b] = run;
+    run += x;
+  }
+  tot[b] = run;
+}
+// per (bucket, chunk): exclusive prefix over warps, in place
+__global__ void k_colscan_c(uint32_t* hist, int G_w, int P, int nchunk, const uint64_t* part) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= P * nchunk) return;
+  const int b = t % P, c = t / P;
+  const int w0 = c * COLCHUNK, w1 = min(G_w, w0 + COLCHUNK);
+  uint64_t run = part[(uint64_t)c * P + b];
+  for (int w = w0; w < w1; ++w) {
+    uint32_t x = hist[(uint64_t)w * P + b];
+    hist[(uint64_t)w * P + b] = (uint32_t)run;
+    run += x;
+  }
+}
+
+// single CTA: exclusive scan of tot[0..P) into bstart[0..P]
+__global__ void __launch_bounds__(1024) k_bucket_scan(const uint64_t* tot, int P, uint64_t* bstart) {
+  __shared__ uint64_t wsum[32];
+  const int t = threadIdx.x;
+  const int per = (P + 1023) / 1024;
+  const int b0 = min(P, t * per), b1 = min(P, b0 + per);
+  uint64_t s = 0;
+  for (int b = b0; b < b1; ++b) s += tot[b];
+  // block exclusive scan of s
+  uint64_t x = s;
+  const int lane = t & 31, w = t >> 5;
+  for (int o = 1; o < 32; o <<= 1) {
+    uint64_t y = __shfl_up_sync(FULL, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    uint64_t z = wsum[lane];
+    for (int o = 1; o < 32; o <<= 1) {
+      uint64_t y = __shfl_up_sync(FULL, z, o);
+      if (lane >= o) z += y;
+    }
+    wsum[lane] = z;
+  }
+  __syncthreads();
+  uint64_t run = x - s + (w ? wsum[w - 1] : 0);
+  for (int b = b0; b < b1; ++b) {
+    bstart[b] = run;
+    run += tot[b];
+  }
+  if (t == 1023) bstart[P] = run;
+}
+
+template <int F>
+__global__ void __launch_bounds__(SC_WARPS * 32)
+k_scatter(const void* keyp, const uint8_t* pred, uint64_t n, uint64_t per_warp, int G_w, int B1, int nq,
+          int n_letters, const uint32_t* pre, const uint64_t* bstart, typename RecT<F>::type* out, Acc* acc) {
+  extern __shared__ uint32_t sm_cur[];
+  typedef typename RecT<F>::type Rec;
+  const int P = 1 << B1;
+  const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * SC_WARPS + wl;
+  if (gw >= G_w) return;
+  uint32_t* cur = sm_cur + wl * P;
+  for (int b = lane; b < P; b += 32) cur[b] = (uint32_t)(bstart[b] + pre[(uint64_t)gw * P + b]);
+  __syncwarp();
+  const uint64_t begin = (uint64_t)gw * per_warp, end = min(n, begin + per_warp);
+  bool bad = false;
+  const uint32_t lt = lanemask_lt();
+  for (uint64_t base = begin; base < end; base += 32) {
+    const uint64_t i = base + lane;
+    const bool v = i < end;
+    uint32_t b = 0xFFFFFFFFu;
+    Rec rec = 0;
+    if (v) {
+      uint32_t letter = pred[i];
+      if (letter >= (uint32_t)n_letters) { bad = true; letter = 0; }
+      Bucketed r = make_record<F>(load_key<F>(keyp, i), letter, B1, nq);
+      b = r.bucket;
+      rec = (Rec)r.rec;
+    }
+    const uint32_t peers = __match_any_sync(FULL, b);
+    uint32_t pos = 0;
+    if (v) pos = cur[b] + __popc(peers & lt);
+    __syncwarp();
+    if (v && lane == __ffs(peers) - 1) cur[b] += __popc(peers);
+    __syncwarp();
+    if (v) out[pos] = rec;
+  }
+  if (__any_sync(FULL, bad) && lane == 0) atomicOr(&acc->err, ERR_LETTER);
+}
+
+// ------------------------------------------------------------------ tiles of buckets
+// Single CTA: split every non-empty bucket b (bstart[b]..bstart[b+1]) into
+// ceil(len / tile_len) tiles; first[b]/K[b] give each bucket's tile range.
+__global__ void __launch_bounds__(1024)
+k_make_tiles(const uint64_t* bstart, int P, uint64_t tile_len, Tile* tiles, uint32_t* first, uint32_t* K,
+             unsigned int* n_tiles) {
+  __shared__ uint32_t wsum[32];
+  const int t = threadIdx.x;
+  const int per = (P + 1023) / 1024;
+  const int b0 = min(P, t * per), b1 = min(P, b0 + per);
+  uint32_t s = 0;
+  for (int b = b0; b < b1; ++b) {
+    uint64_t len = bstart[b + 1] - bstart[b];
+    s += (uint32_t)((len + tile_len - 1) / tile_len);
+  }
+  uint32_t x = s;
+  const int lane = t & 31, w = t >> 5;
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(FULL, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    uint32_t z = wsum[lane];
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(FULL, z, o);
+      if (lane >= o) z += y;
+    }
+    wsum[lane] = z;
+  }
+  __syncthreads();
+  uint32_t run = x - s + (w ? wsum[w - 1] : 0);
+  for (int b = b0; b < b1; ++b) {
+    const uint64_t lo = bstart[b], len = bstart[b + 1] - lo;
+    const uint32_t k = (uint32_t)((len + tile_len - 1) / tile_len);
+    first[b] = run;
+    K[b] = k;
+    for (uint32_t j = 0; j < k; ++j) {
+      Tile tl;
+      tl.bucket = (uint32_t)b; tl.k = j; tl.K = k; tl.pad = 0;
+      tl.begin = lo + j * tile_len;
+      tl.end = min(lo + len, tl.begin + tile_len);
+      tiles[run + j] = tl;
+    }
+    run += k;
+  }
+  if (t == 1023) *n_tiles = run;
+}
+
+// ------------------------------------------------------------------ level-2 multisplit
+template <int F>
+__global__ void __launch_bounds__(SC_WARPS * 32)
+k_hist2(const typename RecT<F>::type* recs, const Tile* tiles, const unsigned int* n_tiles, int B1, int B2,
+        uint32_t* hist2) {
+  __shared__ uint32_t cnt_all[SC_WARPS][64];
+  const int P2 = 1 << B2;
+  const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t tile = blockIdx.x * SC_WARPS + wl;
+  if (tile >= *n_tiles) return;
+  uint32_t* cnt = cnt_all[wl];
+  for (int b = lane; b < P2; b += 32) cnt[b] = 0;
+  __syncwarp();
+  const Tile tl = tiles[tile];
+  const int sh = sub_shift<F>(B1, B2);
+  for (uint64_t base = tl.begin; base < tl.end; base += 32) {
+    const uint64_t i = base + lane;
+    const bool v = i < tl.end;
+    uint32_t b = 0xFFFFFFFFu;
+    if (v) b = (uint32_t)((uint64_t)recs[i] >> sh) & (P2 - 1);
+    const uint32_t peers = __match_any_sync(FULL, b);
+    if (v && lane == __ffs(peers) - 1) cnt[b] += __popc(peers);
+    __syncwarp();
+  }
+  for (int b = lane; b < P2; b += 32) hist2[(uint64_t)tile * P2 + b] = cnt[b];
+}
+
+// per (first-level bucket, sub-bucket): exclusive prefix over the bucket's tiles
+__global__ void k_scan2(uint32_t* hist2, const uint32_t* tfirst, const uint32_t* tK, int P1, int B2, uint64_t* tot2) {
+  const int P2 = 1 << B2;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= P1 * P2) return;
+  const int b1 = t >> B2, b2 = t & (P2 - 1);
+  const uint32_t f = tfirst[b1], k = tK[b1];
+  uint64_t run = 0;
+  for (uint32_t j = 0; j < k; ++j) {
+    uint32_t x = hist2[(uint64_t)(f + j) * P2 + b2];
+    hist2[(uint64_t)(f + j) * P2 + b2] = (uint32_t)run;
+    run += x;
+  }
+  tot2[t] = run;
+}
+
+template <int F>
+__global__ void __launch_bounds__(SC_WARPS * 32)
+k_scatter2(const typename RecT<F>::type* in, const Tile* tiles, const unsigned int* n_tiles, int B1, int B2,
+           const uint32_t* pre2, const uint64_t* bstart2, typename RecT<F>::type* out) {
+  __shared__ uint32_t cur_all[SC_WARPS][64];
+  const int P2 = 1 << B2;
+  const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t tile = blockIdx.x * SC_WARPS + wl;
+  if (tile >= *n_tiles) return;
+  const Tile tl = tiles[tile];
+  uint32_t* cur = cur_all[wl];
+  for (int b = lane; b < P2; b += 32)
+    cur[b] = (uint32_t)(bstart2[((uint64_t)tl.bucket << B2) + b] + pre2[(uint64_t)tile * P2 + b]);
+  __syncwarp();
+  const int sh = sub_shift<F>(B1, B2);
+  const uint32_t lt = lanemask_lt();
+  for (uint64_t base = tl.begin; base < tl.end; base += 32) {
+    const uint64_t i = base + lane;
+    const bool v = i < tl.end;
+    uint32_t b = 0xFFFFFFFFu;
+    typename RecT<F>::type rec = 0;
+    if (v) { rec = in[i]; b = (uint32_t)((uint64_t)rec >> sh) & (P2 - 1); }
+    const uint32_t peers = __match_any_sync(FULL, b);
+    uint32_t pos = 0;
+    if (v) pos = cur[b] + __popc(peers & lt);
+    __syncwarp();
+    if (v && lane == __ffs(peers) - 1) cur[b] += __popc(peers);
+    __syncwarp();
+    if (v) out[pos] = rec;
+  }
+}
+
+// ------------------------------------------------------------------ fold / combine shared state
+struct SlotTable {
+  uint64_t tkey[HT_CAP];
+  uint16_t tslot[HT_CAP];
+  uint64_t skey[SLOTS];
+  unsigned int nslots;
+  unsigned int ovf;
+};
+
+struct OuterTable {
+  uint32_t ukey[UCAP];
+  uint32_t ucnt[UCAP][6];
+  unsigned int nu;
+  unsigned int ovf;
+};
+
+struct FinalCtx {
+  unsigned long long h0[6], h1[6];
+  unsigned long long nodes0, nodes1;
+};
+
+struct Params {
+  MonitorTab tab;
+  int B1, B2, nq;
+  Acc* acc;
+  rv_bindings out;
+};
+
+__device__ __forceinline__ uint64_t key_mult(uint64_t key) { return key * 0x9E3779B97F4A7C15ull; }
+
+__device__ __forceinline__ bool in_pass(uint64_t key, int bits, uint32_t value) {
+  if (bits == 0) return true;
+  return (uint32_t)((key_mult(key) >> 20) & ((1u << bits) - 1)) == value;
+}
+
+// Find the slot of key, inserting it if absent.  `init` runs once for a new
+// slot before the slot becomes visible.  Returns -1 when the table is full.
+template <typename Init>
+__device__ __forceinline__ int find_or_insert(SlotTable& T, uint64_t key, Acc* acc, Init init) {
+  uint32_t h = (uint32_t)(key_mult(key) >> (64 - HT_BITS));
+  volatile uint64_t* vk = T.tkey;
+  volatile uint16_t* vs = T.tslot;
+  for (int probe = 0; probe < HT_CAP; ++probe) {
+    uint64_t k = vk[h];
+    if (k == EMPTY_KEY) {
+      unsigned long long prev = atomicCAS((unsigned long long*)&T.tkey[h], (unsigned long long)EMPTY_KEY,
+                                          (unsigned long long)key);
+      if (prev == EMPTY_KEY) {
+        unsigned int s = atomicAdd(&T.nslots, 1u);
+        if (s >= SLOTS) {
+          T.ovf = 1;
+          __threadfence_block();
+          vs[h] = FULL_SLOT;
+          return -1;
+        }
+        T.skey[s] = key;
+        init(s);
+        __threadfence_block();
+        vs[h] = (uint16_t)s;
+        return (int)s;
+      }
+      k = prev;
+    }
+    if (k == key) {
+      uint16_t s;
+      int spins = 0;
+      while ((s = vs[h]) == NO_SLOT) {
+        if (++spins > SPIN_LIMIT) { atomicOr(&acc->err, ERR_SPIN); return -1; }
+      }
+      return s == FULL_SLOT ? -1 : (int)s;
+    }
+    h = (h + 1) & (HT_CAP - 1);
+  }
+  T.ovf = 1;
+  return -1;
+}
+
+__device__ void reset_table(SlotTable& T) {
+  for (int i = threadIdx.x; i < HT_CAP; i += blockDim.x) { T.tkey[i] = EMPTY_KEY; T.tslot[i] = NO_SLOT; }
+  if (threadIdx.x == 0) { T.nslots = 0; T.ovf = 0; }
+}
+
+__device__ void reset_outer(OuterTable& U) {
+  for (int i = threadIdx.x; i < UCAP; i += blockDim.x) {
+    U.ukey[i] = 0xFFFFFFFFu;
+    for (int v = 0; v < 6; ++v) U.ucnt[i][v] = 0;
+  }
+  if (threadIdx.x == 0) { U.nu = 0; U.ovf = 0; }
+}
+
+// linear search is enough: an outer table holds the few outer values of one bucket
+__device__ int outer_slot(OuterTable& U, uint32_t u_local) {
+  for (int attempt = 0; attempt < 2 * UCAP; ++attempt) {
+    const unsigned int nu = min(*(volatile unsigned int*)&U.nu, (unsigned int)UCAP);
+    for (unsigned int i = 0; i < nu; ++i) {
+      uint32_t k;
+      int spins = 0;
+      while ((k = *(volatile uint32_t*)&U.ukey[i]) == 0xFFFFFFFFu) {
+        if (++spins > SPIN_LIMIT) return -1;
+      }
+      if (k == (u_local | 0x80000000u)) return (int)i;
+    }
+    // claim the next entry; ukey holds u_local with the top bit set once valid
+    unsigned int i = atomicCAS(&U.nu, nu, nu + 1);
+    if (i == nu) {
+      if (nu >= UCAP) { U.ovf = 1; return -1; }
+      __threadfence_block();
+      *(volatile uint32_t*)&U.ukey[nu] = u_local | 0x80000000u;
+      return (int)nu;
+    }
+  }
+  return -1;
+}
+
+// verdict of one innermost binding whose composed map over its whole cluster is M
+template <int F>
+__device__ __forceinline__ void finalize_slot(const Params& p, FinalCtx& fc, OuterTable& U, uint64_t skey,
+                                              uint64_t M, uint32_t bucket) {
+  const uint32_t state = (uint32_t)((M >> (4 * p.tab.q0)) & 15ull);
+  const uint32_t v = p.tab.labels[state];
+  const uint32_t b1 = bucket >> p.B2;
+  if (p.nq <= 1) {
+    atomicAdd(&fc.h0[v], 1ull);
+    atomicAdd(&fc.nodes0, 1ull);
+  } else {
+    atomicAdd(&fc.h1[v], 1ull);
+    atomicAdd(&fc.nodes1, 1ull);
+    int ui = outer_slot(U, (uint32_t)(skey >> 32));
+    if (ui < 0) atomicOr(&p.acc->err, ERR_OUTER_FULL);
+    else atomicAdd(&U.ucnt[ui][v], 1u);
+  }
+  if (p.out.keys) {
+    unsigned long long idx = atomicAdd(&p.acc->n_out, 1ull);
+    if (idx < p.out.capacity) {
+      p.out.keys[idx] = original_key<F>(skey, b1, p.B1, p.nq);
+      p.out.verdicts[idx] = (uint8_t)v;
+    }
+  }
+}
+
+// after all innermost bindings of a bucket: valuate its outer nodes (level 1)
+template <int F>
+__device__ void finalize_outer(const Params& p, FinalCtx& fc, OuterTable& U, uint32_t bucket) {
+  if (p.nq != 2) return;
+  const unsigned int nu = min(U.nu, (unsigned int)UCAP);
+  const uint32_t b1 = bucket >> p.B2;
+  for (unsigned int i = threadIdx.x; i < nu; i += blockDim.x) {
+    uint64_t v6[6];
+    for (int v = 0; v < 6; ++v) v6[v] = U.ucnt[i][v];
+    const int vd = rvv::valuate(p.tab.q[1].kind, p.tab.q[1].op, p.tab.q[1].num, p.tab.q[1].den, v6);
+    atomicAdd(&fc.h0[vd], 1ull);
+    atomicAdd(&fc.nodes0, 1ull);
+    if (p.out.outer_keys) {
+      unsigned long long idx = atomicAdd(&p.acc->n_out_outer, 1ull);
+      if (idx < p.out.outer_capacity) {
+        p.out.outer_keys[idx] = original_outer<F>(U.ukey[i] & 0x7FFFFFFFu, b1, p.B1);
+        p.out.outer_verdicts[idx] = (uint8_t)vd;
+      }
+    }
+  }
+}
+
+__device__ void flush_final(const Params& p, FinalCtx& fc) {
+  if (threadIdx.x < 6) {
+    if (fc.h0[threadIdx.x]) atomicAdd(&p.acc->level_counts[0][threadIdx.x], fc.h0[threadIdx.x]);
+    if (fc.h1[threadIdx.x]) atomicAdd(&p.acc->level_counts[1][threadIdx.x], fc.h1[threadIdx.x]);
+  }
+  if (threadIdx.x == 0) {
+    if (fc.nodes0) atomicAdd(&p.acc->n_nodes[0], fc.nodes0);
+    if (fc.nodes1) atomicAdd(&p.acc->n_nodes[1], fc.nodes1);
+  }
+}
+
+// ------------------------------------------------------------------ fold
+struct FoldShared {
+  uint64_t lmap[RV_MAX_LETTERS];
+  uint64_t wmap[FOLD_WARPS][SLOTS];
+  SlotTable T;
+  OuterTable U;
+  FinalCtx fc;
+  uint8_t stage[FOLD_WARPS][32];
+  uint32_t pass_bits[64], pass_val[64];
+  int npass;
+  uint64_t item_off;
+  uint32_t item_cnt;
+};
+
+template <int F>
+__global__ void __launch_bounds__(FOLD_THREADS, 2)
+k_fold(const typename RecT<F>::type* recs, const Tile* units, const unsigned int* n_units, Params p,
+       Item* items, Pair* pool) {
+  extern __shared__ __align__(16) unsigned char fold_smem[];
+  FoldShared& S = *reinterpret_cast<FoldShared*>(fold_smem);
+  const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ns = p.tab.n_states;
+  for (int i = threadIdx.x; i < RV_MAX_LETTERS; i += blockDim.x) S.lmap[i] = p.tab.maps[i];
+  if (threadIdx.x < 6) { S.fc.h0[threadIdx.x] = 0; S.fc.h1[threadIdx.x] = 0; }
+  if (threadIdx.x == 0) { S.fc.nodes0 = 0; S.fc.nodes1 = 0; }
+  const unsigned int nun = *n_units;
+  for (unsigned int u = blockIdx.x; u < nun; u += gridDim.x) {
+    const Tile t = units[u];
+    const bool single = t.K == 1;
+    const uint64_t len = t.end - t.begin;
+    const uint64_t chunk = (len + FOLD_WARPS - 1) / FOLD_WARPS;
+    const uint64_t wbeg = t.begin + min(len, chunk * wl), wend = t.begin + min(len, chunk * (wl + 1));
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      S.npass = 1; S.pass_bits[0] = 0; S.pass_val[0] = 0;
+      S.item_cnt = 0;
+      S.item_off = single ? 0 : atomicAdd(&p.acc->pair_top[0], (unsigned long long)len);
+    }
+    if (t.k == 0) reset_outer(S.U);
+    __syncthreads();
+    while (true) {
+      __syncthreads();
+      if (S.npass == 0) break;
+      const int bits = (int)S.pass_bits[S.npass - 1];
+      const uint32_t val = S.pass_val[S.npass - 1];
+      reset_table(S.T);
+      __syncthreads();
+      for (uint64_t base = wbeg; base < wend; base += 32) {
+        const uint64_t i = base + lane;
+        const bool v = i < wend;
+        uint64_t rec = v ? (uint64_t)recs[i] : 0;
+        const uint64_t key = rec >> 8;
+        int slot = -1;
+        if (v && in_pass(key, bits, val)) {
+          slot = find_or_insert(S.T, key, p.acc, [&](unsigned int s) {
+            for (int w = 0; w < FOLD_WARPS; ++w) S.wmap[w][s] = IDENTITY_MAP;
+          });
+        }
+        const uint32_t peers = __match_any_sync(FULL, slot);
+        S.stage[wl][lane] = (uint8_t)(rec & 0xFF);
+        __syncwarp();
+        if (slot >= 0 && lane == __ffs(peers) - 1) {
+          uint64_t M = S.wmap[wl][slot];
+          uint32_t m = peers;
+          while (m) {
+            const int j = __ffs(m) - 1;
+            m &= m - 1;
+            M = apply_map(M, S.lmap[S.stage[wl][j]], ns);
+          }
+          S.wmap[wl][slot] = M;
+        }
+        __syncwarp();
+      }
+      __syncthreads();
+      if (S.T.ovf) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          // split this pass into two halves on one more key bit
+          S.npass -= 1;
+          if (bits >= 20 || S.npass + 2 > 64) {
+            atomicOr(&p.acc->err, ERR_SPIN);
+            S.npass = 0;
+          } else {
+            S.pass_bits[S.npass] = bits + 1; S.pass_val[S.npass] = val;
+            S.pass_bits[S.npass + 1] = bits + 1; S.pass_val[S.npass + 1] = val | (1u << bits);
+            S.npass += 2;
+          }
+        }
+        continue;
+      }
+      const unsigned int nsl = min(S.T.nslots, (unsigned int)SLOTS);
+      for (unsigned int s = threadIdx.x; s < nsl; s += blockDim.x) {
+        uint64_t M = S.wmap[0][s];
+        for (int w = 1; w < FOLD_WARPS; ++w) M = apply_map(M, S.wmap[w][s], ns);
+        if (single) finalize_slot<F>(p, S.fc, S.U, S.T.skey[s], M, t.bucket);
+        else pool[S.item_off + S.item_cnt + s] = Pair{S.T.skey[s], M};
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) { S.item_cnt += nsl; S.npass -= 1; }
+    }
+    __syncthreads();
+    if (single) finalize_outer<F>(p, S.fc, S.U, t.bucket);
+    else if (threadIdx.x == 0) items[u] = Item{S.item_off, S.item_cnt, 0};
+  }
+  __syncthreads();
+  flush_final(p, S.fc);
+}
+
+// Single CTA: groups of up to GC consecutive items of every bucket still
+// holding K >= 2 items; a group whose bucket ends up with one group is final.
+__global__ void __launch_bounds__(1024)
+k_make_groups(const uint32_t* first_in, const uint32_t* K_in, int P, Group* groups, uint32_t* first_out,
+              uint32_t* K_out, unsigned int* n_groups) {
+  __shared__ uint32_t wsum[32];
+  const int t = threadIdx.x;
+  const int per = (P + 1023) / 1024;
+  const int b0 = min(P, t * per), b1 = min(P, b0 + per);
+  uint32_t s = 0;
+  for (int b = b0; b < b1; ++b) if (K_in[b] >= 2) s += (K_in[b] + GC - 1) / GC;
+  uint32_t x = s;
+  const int lane = t & 31, w = t >> 5;
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(FULL, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    uint32_t z = wsum[lane];
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(FULL, z, o);
+      if (lane >= o) z += y;
+    }
+    wsum[lane] = z;
+  }
+  __syncthreads();
+  uint32_t run = x - s + (w ? wsum[w - 1] : 0);
+  for (int b = b0; b < b1; ++b) {
+    const uint32_t k = K_in[b];
+    if (k < 2) { first_out[b] = 0; K_out[b] = k == 1 ? 0 : 0; continue; }
+    const uint32_t g = (k + GC - 1) / GC;
+    first_out[b] = run;
+    K_out[b] = g;
+    for (uint32_t j = 0; j < g; ++j) {
+      Group G;
+      G.bucket = (uint32_t)b;
+      G.first = first_in[b] + j * GC;
+      G.cnt = min((uint32_t)GC, k - j * GC);
+      G.k = j; G.K = g; G.pad = 0;
+      groups[run + j] = G;
+    }
+    run += g;
+  }
+  if (t == 1023) *n_groups = run;
+}
+
+struct CombineShared {
+  uint64_t smap[SLOTS];
+  SlotTable T;
+  OuterTable U;
+  FinalCtx fc;
+  uint32_t pass_bits[64], pass_val[64];
+  int npass;
+  uint64_t out_off;
+  uint32_t out_cnt;
+};
+
+template <int F>
+__global__ void __launch_bounds__(FOLD_THREADS)
+k_combine(const Item* items_in, const Pair* pool_in, const Group* groups, const unsigned int* n_groups,
+          Params p, Item* items_out, Pair* pool_out, int dst) {
+  extern __shared__ __align__(16) unsigned char comb_smem[];
+  CombineShared& S = *reinterpret_cast<CombineShared*>(comb_smem);
+  const int ns = p.tab.n_states;
+  if (threadIdx.x < 6) { S.fc.h0[threadIdx.x] = 0; S.fc.h1[threadIdx.x] = 0; }
+  if (threadIdx.x == 0) { S.fc.nodes0 = 0; S.fc.nodes1 = 0; }
+  const unsigned int ng = *n_groups;
+  for (unsigned int g = blockIdx.x; g < ng; g += gridDim.x) {
+    const Group G = groups[g];
+    const bool final_ = G.K == 1;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint64_t total = 0;
+      for (uint32_t j = 0; j < G.cnt; ++j) total += items_in[G.first + j].cnt;
+      S.npass = 1; S.pass_bits[0] = 0; S.pass_val[0] = 0;
+      S.out_cnt = 0;
+      S.out_off = final_ ? 0 : atomicAdd(&p.acc->pair_top[dst], (unsigned long long)total);
+    }
+    reset_outer(S.U);
+    __syncthreads();
+    while (true) {
+      __syncthreads();
+      if (S.npass == 0) break;
+      const int bits = (int)S.pass_bits[S.npass - 1];
+      const uint32_t val = S.pass_val[S.npass - 1];
+      reset_table(S.T);
+      __syncthreads();
+      for (uint32_t j = 0; j < G.cnt; ++j) {
+        const Item I = items_in[G.first + j];
+        for (uint32_t q = threadIdx.x; q < I.cnt; q += blockDim.x) {
+          const Pair pr = pool_in[I.off + q];
+          if (!in_pass(pr.key, bits, val)) continue;
+          const int slot = find_or_insert(S.T, pr.key, p.acc, [&](unsigned int s) { S.smap[s] = IDENTITY_MAP; });
+          if (slot >= 0) S.smap[slot] = apply_map(S.smap[slot], pr.map, ns);
+        }
+        __syncthreads();
+      }
+      if (S.T.ovf) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          S.npass -= 1;
+          if (bits >= 20 || S.npass + 2 > 64) {
+            atomicOr(&p.acc->err, ERR_SPIN);
+            S.npass = 0;
+          } else {
+            S.pass_bits[S.npass] = bits + 1; S.pass_val[S.npass] = val;
+            S.pass_bits[S.npass + 1] = bits + 1; S.pass_val[S.npass + 1] = val | (1u << bits);
+            S.npass += 2;
+          }
+        }
+        continue;
+      }
+      const unsigned int nsl = min(S.T.nslots, (unsigned int)SLOTS);
+      for (unsigned int s = threadIdx.x; s < nsl; s += blockDim.x) {
+        if (final_) finalize_slot<F>(p, S.fc, S.U, S.T.skey[s], S.smap[s], G.bucket);
+        else pool_out[S.out_off + S.out_cnt + s] = Pair{S.T.skey[s], S.smap[s]};
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) { S.out_cnt += nsl; S.npass -= 1; }
+    }
+    __syncthreads();
+    if (final_) finalize_outer<F>(p, S.fc, S.U, G.bucket);
+    else if (threadIdx.x == 0) items_out[g] = Item{S.out_off, S.out_cnt, 0};
+  }
+  __syncthreads();
+  flush_final(p, S.fc);
+}
+
+__global__ void k_root(const Acc* acc, Params p, uint64_t n, rv_result* out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  rv_result r;
+  memset(&r, 0, sizeof r);
+  for (int m = 0; m < 2; ++m) {
+    for (int v = 0; v < 6; ++v) r.level_counts[m][v] = acc->level_counts[m][v];
+    r.n_nodes[m] = acc->n_nodes[m];
+  }
+  r.events = n;
+  uint64_t v6[6];
+  for (int v = 0; v < 6; ++v) v6[v] = acc->level_counts[0][v];
+  if (p.nq == 0) {
+    r.root = RV_BOT;
+    for (int v = 0; v < 6; ++v) if (v6[v]) r.root = v;
+  } else {
+    for (int v = 0; v < 6; ++v) r.root_counts[v] = v6[v];
+    r.root = rvv::valuate(p.tab.q[0].kind, p.tab.q[0].op, p.tab.q[0].num, p.tab.q[0].den, v6);
+  }
+  const unsigned int e = acc->err;
+  r.status = RV_OK;
+  if (e & (ERR_LETTER | ERR_TS)) r.status = RV_EINVAL;
+  else if (e & ERR_OUTER_FULL) r.status = RV_EAGAIN;   // host retries with a finer split
+  else if (e) r.status = RV_EINTERNAL;
+  *out = r;
+}
+
+// ------------------------------------------------------------------ host side
+struct Plan {
+  int F, B1, B2, P1, P, G_w, nchunk;
+  uint64_t n, per_warp, unit;
+  uint64_t max_tiles2, max_units;
+  int levels;
+  size_t rec_bytes;
+  // workspace offsets
+  size_t o_acc, o_hist, o_part, o_tot1, o_bstart1, o_recA, o_recB, o_tiles2, o_tf2, o_tk2, o_hist2, o_tot2,
+      o_bstart2, o_units, o_uf, o_uk, o_items0, o_items1, o_groups, o_gf0, o_gk0, o_gf1, o_gk1, o_pool0,
+      o_pool1, o_res, o_hkey, o_hpred, o_hts, total;
+};
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static int num_sms() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      sms = 148;
+  }
+  return sms;
+}
+
+static Plan make_plan(const rv_formula* f, uint64_t n, int host_input, const rv_verify_opts* o, int extra_b2) {
+  Plan pl{};
+  pl.n = n;
+  pl.F = f->n_quant == 2 ? FMT_K2 : (f->key_bits == 64 && f->n_quant == 1 ? FMT_K64 : FMT_K32);
+  int b1 = o && o->bucket_bits ? o->bucket_bits : 0;
+  if (!b1) {
+    b1 = 8;
+    while (b1 < 11 && (n >> b1) > 32768) ++b1;
+  }
+  pl.B1 = std::min(11, std::max(8, b1));
+  pl.P1 = 1 << pl.B1;
+  int b2 = o && o->sub_bucket_bits >= 0 ? o->sub_bucket_bits : 0;
+  if (!(o && o->sub_bucket_bits) && f->n_quant == 2) {
+    b2 = 0;
+    while (b2 < 6 && (n >> (pl.B1 + b2)) > 8192) ++b2;
+  }
+  b2 += extra_b2;
+  pl.B2 = std::min(6, std::max(0, b2));
+  pl.P = pl.P1 << pl.B2;
+  pl.unit = o && o->unit_records ? (uint64_t)o->unit_records : 32768;
+  pl.unit = std::max<uint64_t>(256, pl.unit);
+  const uint64_t max_w = (uint64_t)num_sms() * 3 * SC_WARPS;
+  uint64_t gw = (n + 2047) / 2048;
+  if (gw > max_w) gw = max_w;
+  if (gw < 1) gw = 1;
+  pl.per_warp = ((n + gw - 1) / gw + 31) / 32 * 32;
+  if (pl.per_warp == 0) pl.per_warp = 32;
+  pl.G_w = (int)((n + pl.per_warp - 1) / pl.per_warp);
+  if (pl.G_w < 1) pl.G_w = 1;
+  pl.nchunk = (pl.G_w + COLCHUNK - 1) / COLCHUNK;
+  pl.max_tiles2 = n / TILE2 + pl.P1 + 1;
+  pl.max_units = n / pl.unit + pl.P + 1;
+  pl.levels = 0;
+  for (uint64_t cap = 1; cap < n / pl.unit + 2; cap *= GC) ++pl.levels;
+  pl.rec_bytes = pl.F == FMT_K32 ? 4 : 8;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t r = off; off = align256(off + bytes); return r; };
+  pl.o_acc = take(sizeof(Acc));
+  pl.o_hist = take((size_t)pl.P1 * pl.G_w * 4);
+  pl.o_part = take((size_t)pl.P1 * pl.nchunk * 8);
+  pl.o_tot1 = take((size_t)pl.P1 * 8);
+  pl.o_bstart1 = take((size_t)(pl.P1 + 1) * 8);
+  pl.o_recA = take(n * pl.rec_bytes);
+  pl.o_recB = pl.B2 ? take(n * pl.rec_bytes) : pl.o_recA;
+  pl.o_tiles2 = pl.B2 ? take(pl.max_tiles2 * sizeof(Tile)) : 0;
+  pl.o_tf2 = pl.B2 ? take((size_t)pl.P1 * 4) : 0;
+  pl.o_tk2 = pl.B2 ? take((size_t)pl.P1 * 4) : 0;
+  pl.o_hist2 = pl.B2 ? take(pl.max_tiles2 * ((size_t)1 << pl.B2) * 4) : 0;
+  pl.o_tot2 = pl.B2 ? take((size_t)pl.P * 8) : 0;
+  pl.o_bstart2 = pl.B2 ? take((size_t)(pl.P + 1) * 8) : pl.o_bstart1;
+  pl.o_units = take(pl.max_units * sizeof(Tile));
+  pl.o_uf = take((size_t)pl.P * 4);
+  pl.o_uk = take((size_t)pl.P * 4);
+  pl.o_items0 = take(pl.max_units * sizeof(Item));
+  pl.o_items1 = take(pl.max_units * sizeof(Item));
+  pl.o_groups = take(pl.max_units * sizeof(Group));
+  pl.o_gf0 = take((size_t)pl.P * 4);
+  pl.o_gk0 = take((size_t)pl.P * 4);
+  pl.o_gf1 = take((size_t)pl.P * 4);
+  pl.o_gk1 = take((size_t)pl.P * 4);
+  pl.o_pool0 = take(std::max<uint64_t>(n, 1) * sizeof(Pair));
+  pl.o_pool1 = take(std::max<uint64_t>(n, 1) * sizeof(Pair));
+  pl.o_res = take(sizeof(rv_result));
+  pl.o_hkey = host_input ? take(n * (f->key_bits / 8)) : 0;
+  pl.o_hpred = host_input ? take(n) : 0;
+  pl.o_hts = host_input ? take(n * 4) : 0;
+  pl.total = off;
+  return pl;
+}
+
+static MonitorTab make_tab(const rv_formula* f) {
+  MonitorTab t;
+  memset(&t, 0, sizeof t);
+  for (int l = 0; l < RV_MAX_LETTERS; ++l) t.maps[l] = l < f->n_letters ? f->maps[l] : IDENTITY_MAP;
+  memcpy(t.labels, f->labels, sizeof t.labels);
+  t.n_states = f->n_states;
+  t.q0 = f->q0;
+  t.n_letters = f->n_letters;
+  t.nq = f->n_quant;
+  t.q[0] = f->q[0];
+  t.q[1] = f->q[1];
+  return t;
+}
+
+#define RV_CU(call)                                                                       \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess) return rv_fail(RV_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+template <int F>
+static rv_status launch_all(const Plan& pl, const rv_formula* f, const void* key, const uint8_t* pred,
+                            const uint32_t* ts, unsigned char* ws, rv_result* dev_out, const rv_bindings* b,
+                            cudaStream_t s) {
+  typedef typename RecT<F>::type Rec;
+  Acc* acc = (Acc*)(ws + pl.o_acc);
+  RV_CU(cudaMemsetAsync(acc, 0, sizeof(Acc), s));
+  Params p;
+  memset(&p, 0, sizeof p);
+  p.tab = make_tab(f);
+  p.B1 = pl.B1;
+  p.B2 = pl.B2;
+  p.nq = f->n_quant;
+  p.acc = acc;
+  if (b) p.out = *b;
+  const uint64_t n = pl.n;
+  if (n > 0) {
+    uint32_t* hist = (uint32_t*)(ws + pl.o_hist);
+    uint64_t* part = (uint64_t*)(ws + pl.o_part);
+    uint64_t* tot1 = (uint64_t*)(ws + pl.o_tot1);
+    uint64_t* bstart1 = (uint64_t*)(ws + pl.o_bstart1);
+    Rec* recA = (Rec*)(ws + pl.o_recA);
+    const int sc_blocks = (pl.G_w + SC_WARPS - 1) / SC_WARPS;
+    const size_t sc_smem = (size_t)SC_WARPS * pl.P1 * 4;
+    RV_LAUNCH("k_hist", k_hist<F>, sc_blocks, SC_WARPS * 32, sc_smem, s, key, ts, n, pl.per_warp, pl.G_w, pl.B1, f->n_quant, hist, acc);
+    const int ct = pl.P1 * pl.nchunk;
+    RV_LAUNCH("k_colscan_a", k_colscan_a, (ct + 255) / 256, 256, 0, s, hist, pl.G_w, pl.P1, pl.nchunk, part);
+    RV_LAUNCH("k_colscan_b", k_colscan_b, (pl.P1 + 255) / 256, 256, 0, s, part, pl.P1, pl.nchunk, tot1);
+    RV_LAUNCH("k_colscan_c", k_colscan_c, (ct + 255) / 256, 256, 0, s, hist, pl.G_w, pl.P1, pl.nchunk, part);
+    RV_LAUNCH("k_bucket_scan", k_bucket_scan, 1, 1024, 0, s, tot1, pl.P1, bstart1);
+    RV_LAUNCH("k_scatter", k_scatter<F>, sc_blocks, SC_WARPS * 32, sc_smem, s, key, pred, n, pl.per_warp, pl.G_w, pl.B1, f->n_quant,
+                                                          f->n_letters, hist, bstart1, recA, acc);
+    Rec* recs = recA;
+    uint64_t* bstart = bstart1;
+    if (pl.B2) {
+      Tile* tiles2 = (Tile*)(ws + pl.o_tiles2);
+      uint32_t* tf2 = (uint32_t*)(ws + pl.o_tf2);
+      uint32_t* tk2 = (uint32_t*)(ws + pl.o_tk2);
+      uint32_t* hist2 = (uint32_t*)(ws + pl.o_hist2);
+      uint64_t* tot2 = (uint64_t*)(ws + pl.o_tot2);
+      uint64_t* bstart2 = (uint64_t*)(ws + pl.o_bstart2);
+      Rec* recB = (Rec*)(ws + pl.o_recB);
+      RV_LAUNCH("k_make_tiles", k_make_tiles, 1, 1024, 0, s, bstart1, pl.P1, TILE2, tiles2, tf2, tk2, &acc->n_tiles2);
+      const int t2_blocks = (int)((pl.max_tiles2 + SC_WARPS - 1) / SC_WARPS);
+      RV_LAUNCH("k_hist2", k_hist2<F>, t2_blocks, SC_WARPS * 32, 0, s, recA, tiles2, &acc->n_tiles2, pl.B1, pl.B2, hist2);
+      RV_LAUNCH("k_scan2", k_scan2, (pl.P + 255) / 256, 256, 0, s, hist2, tf2, tk2, pl.P1, pl.B2, tot2);
+      RV_LAUNCH("k_bucket_scan", k_bucket_scan, 1, 1024, 0, s, tot2, pl.P, bstart2);
+      RV_LAUNCH("k_scatter2", k_scatter2<F>, t2_blocks, SC_WARPS * 32, 0, s, recA, tiles2, &acc->n_tiles2, pl.B1, pl.B2, hist2, bstart2, recB);
+      recs = recB;
+      bstart = bstart2;
+    }
+    Tile* units = (Tile*)(ws + pl.o_units);
+    uint32_t* uf = (uint32_t*)(ws + pl.o_uf);
+    uint32_t* uk = (uint32_t*)(ws + pl.o_uk);
+    Item* items0 = (Item*)(ws + pl.o_items0);
+    Item* items1 = (Item*)(ws + pl.o_items1);
+    Group* groups = (Group*)(ws + pl.o_groups);
+    Pair* pool0 = (Pair*)(ws + pl.o_pool0);
+    Pair* pool1 = (Pair*)(ws + pl.o_pool1);
+    RV_LAUNCH("k_make_tiles", k_make_tiles, 1, 1024, 0, s, bstart, pl.P, pl.unit, units, uf, uk, &acc->n_units);
+    const int grid = (int)std::min<uint64_t>(pl.max_units, (uint64_t)num_sms() * 2);
+    RV_LAUNCH("k_fold", k_fold<F>, grid, FOLD_THREADS, sizeof(FoldShared), s, recs, units, &acc->n_units, p, items0, pool0);
+    const uint32_t* fin = uf;
+    const uint32_t* kin = uk;
+    uint32_t* gf[2] = {(uint32_t*)(ws + pl.o_gf0), (uint32_t*)(ws + pl.o_gf1)};
+    uint32_t* gk[2] = {(uint32_t*)(ws + pl.o_gk0), (uint32_t*)(ws + pl.o_gk1)};
+    Item* iin = items0;
+    Item* iout = items1;
+    Pair* pin = pool0;
+    Pair* pout = pool1;
+    for (int l = 0; l < pl.levels; ++l) {
+      const int dst = (l + 1) & 1;
+      RV_CU(cudaMemsetAsync(&acc->pair_top[dst], 0, sizeof(unsigned long long), s));
+      RV_LAUNCH("k_make_groups", k_make_groups, 1, 1024, 0, s, fin, kin, pl.P, groups, gf[l & 1], gk[l & 1], &acc->n_groups[l]);
+      const int cgrid = (int)std::min<uint64_t>(pl.max_units / GC + pl.P, (uint64_t)num_sms() * 2);
+      RV_LAUNCH("k_combine", k_combine<F>, cgrid, FOLD_THREADS, sizeof(CombineShared), s, iin, pin, groups, &acc->n_groups[l], p,
+                                                                      iout, pout, dst);
+      fin = gf[l & 1];
+      kin = gk[l & 1];
+      std::swap(iin, iout);
+      std::swap(pin, pout);
+    }
+  }
+  RV_LAUNCH("k_root", k_root, 1, 32, 0, s, acc, p, n, dev_out);
+  RV_CU(cudaGetLastError());
+  return RV_OK;
+}
+
+static bool g_attr_done[3];
+
+template <int F>
+static rv_status set_attrs() {
+  if (g_attr_done[F]) return RV_OK;
+  RV_CU(cudaFuncSetAttribute(k_fold<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(FoldShared)));
+  RV_CU(cudaFuncSetAttribute(k_combine<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(CombineShared)));
+  RV_CU(cudaFuncSetAttribute(k_hist<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, SC_WARPS * 2048 * 4));
+  RV_CU(cudaFuncSetAttribute(k_scatter<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, SC_WARPS * 2048 * 4));
+  g_attr_done[F] = true;
+  return RV_OK;
+}
+
+static rv_status dispatch(const Plan& pl, const rv_formula* f, const void* key, const uint8_t* pred, const uint32_t* ts,
+                          unsigned char* ws, rv_result* dev_out, const rv_bindings* b, cudaStream_t s) {
+  rv_status st;
+  switch (pl.F) {
+    case FMT_K32: st = set_attrs<FMT_K32>(); if (st) return st; return launch_all<FMT_K32>(pl, f, key, pred, ts, ws, dev_out, b, s);
+    case FMT_K64: st = set_attrs<FMT_K64>(); if (st) return st; return launch_all<FMT_K64>(pl, f, key, pred, ts, ws, dev_out, b, s);
+    default: st = set_attrs<FMT_K2>(); if (st) return st; return launch_all<FMT_K2>(pl, f, key, pred, ts, ws, dev_out, b, s);
+  }
+}
+
+rv_alloc_fn g_alloc = nullptr;
+rv_free_fn g_free = nullptr;
+void* g_alloc_ctx = nullptr;
+
+}  // namespace
+
+// allocator hooks (also used by the streaming service)
+void* rv_dev_alloc(size_t bytes) {
+  if (g_alloc) return g_alloc(bytes, g_alloc_ctx);
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+  return p;
+}
+void rv_dev_free(void* p) {
+  if (!p) return;
+  if (g_free) g_free(p, g_alloc_ctx);
+  else cudaFree(p);
+}
+
+extern "C" void rv_set_allocator(rv_alloc_fn alloc, rv_free_fn free_fn, void* ctx) {
+  g_alloc = alloc;
+  g_free = free_fn;
+  g_alloc_ctx = ctx;
+}
+
+extern "C" size_t rv_verify_workspace_size(const rv_formula* f, uint64_t n, int host_input, const rv_verify_opts* opts) {
+  if (!f) return 0;
+  size_t worst = 0;
+  for (int extra = 0; extra <= 6; extra += 2) worst = std::max(worst, make_plan(f, n, host_input, opts, extra).total);
+  return worst;
+}
+
+static rv_status check_args(const rv_formula* f, const rv_trace* t) {
+  if (!f || !t) return rv_fail(RV_EINVAL, "null formula or trace");
+  if (t->n > 0xFFFFFFFFull) return rv_fail(RV_EINVAL, "traces are limited to 2^32-1 events");
+  if (t->n && (!t->key || !t->pred)) return rv_fail(RV_EINVAL, "null key or pred array");
+  if (f->n_quant == 0 && t->n == 0) return rv_fail(RV_EINVAL, "an unquantified property needs a non-empty trace");
+  return RV_OK;
+}
+
+extern "C" rv_status rv_verify_trace_async(const rv_formula* f, const rv_trace* t, void* ws, size_t ws_bytes,
+                                           rv_result* dev_out, const rv_bindings* bindings,
+                                           const rv_verify_opts* opts, cudaStream_t s) {
+  rv_status st = check_args(f, t);
+  if (st) return st;
+  if (!ws || !dev_out) return rv_fail(RV_EINVAL, "the asynchronous form needs a workspace and a device result");
+  Plan pl = make_plan(f, t->n, 0, opts, 0);
+  if (ws_bytes < pl.total) return rv_fail(RV_ENOMEM, "workspace of %zu bytes, need %zu", ws_bytes, pl.total);
+  return dispatch(pl, f, t->key, t->pred, t->ts, (unsigned char*)ws, dev_out, bindings, s);
+}
+
+extern "C" rv_status rv_verify_trace(const rv_formula* f, const rv_trace* t, int on_device, void* ws, size_t ws_bytes,
+                                     rv_result* out, const rv_bindings* bindings, const rv_verify_opts* opts,
+                                     cudaStream_t s) {
+  rv_status st = check_args(f, t);
+  if (st) return st;
+  if (!out) return rv_fail(RV_EINVAL, "null result");
+  static thread_local rv_result* pinned = nullptr;
+  if (!pinned && cudaMallocHost(&pinned, sizeof(rv_result)) != cudaSuccess)
+    return rv_fail(RV_ECUDA, "cannot allocate pinned result buffer");
+  for (int extra = 0; extra <= 6; extra += 2) {
+    Plan pl = make_plan(f, t->n, !on_device, opts, extra);
+    unsigned char* w = (unsigned char*)ws;
+    bool owned = false;
+    if (!w) {
+      w = (unsigned char*)rv_dev_alloc(pl.total);
+      if (!w) return rv_fail(RV_ENOMEM, "cannot allocate %zu bytes of workspace", pl.total);
+      owned = true;
+    } else if (ws_bytes < pl.total) {
+      return rv_fail(RV_ENOMEM, "workspace of %zu bytes, need %zu", ws_bytes, pl.total);
+    }
+    const void* key = t->key;
+    const uint8_t* pred = t->pred;
+    const uint32_t* ts = t->ts;
+    st = RV_OK;
+    if (!on_device && t->n) {
+      const size_t kb = (size_t)t->n * (f->key_bits / 8);
+      if (cudaMemcpyAsync(w + pl.o_hkey, t->key, kb, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+          cudaMemcpyAsync(w + pl.o_hpred, t->pred, t->n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+          (t->ts && cudaMemcpyAsync(w + pl.o_hts, t->ts, t->n * 4, cudaMemcpyHostToDevice, s) != cudaSuccess))
+        st = rv_fail(RV_ECUDA, "host-to-device copy failed");
+      key = w + pl.o_hkey;
+      pred = w + pl.o_hpred;
+      ts = t->ts ? (const uint32_t*)(w + pl.o_hts) : nullptr;
+    }
+    rv_result* dres = (rv_result*)(w + pl.o_res);
+    if (!st) st = dispatch(pl, f, key, pred, ts, w, dres, bindings, s);
+    if (!st && cudaMemcpyAsync(pinned, dres, sizeof(rv_result), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+      st = rv_fail(RV_ECUDA, "device-to-host copy failed");
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (!st && e != cudaSuccess) st = rv_fail(RV_ECUDA, "stream synchronize: %s", cudaGetErrorString(e));
+    if (owned) rv_dev_free(w);
+    if (st) return st;
+    *out = *pinned;
+    if (out->status == RV_EAGAIN && f->n_quant == 2 && pl.B2 < 6 && !(opts && opts->sub_bucket_bits)) continue;
+    if (out->status == RV_EINVAL) return rv_fail(RV_EINVAL, "trace rejected: predicate code out of range or timestamps decreasing");
+    if (out->status != RV_OK) return rv_fail((rv_status)out->status, "device status %d", out->status);
+    return RV_OK;
+  }
+  return rv_fail(RV_EINTERNAL, "too many outer bindings per bucket even at the finest split");
+}

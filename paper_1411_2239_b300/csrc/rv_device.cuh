@@ -1,0 +1,161 @@
+// Device building blocks shared by the offline, batched and streaming paths.
+#pragma once
+#include <stdint.h>
+#include <cuda_runtime.h>
+
+#include "rv_internal.h"
+#include "valuate.h"
+
+namespace rvd {
+
+// ------------------------------------------------------------------ bijective key mixing
+// MurmurHash3 finalisers (public domain).  Both are bijections, so the bits of
+// a mixed key that are not spent on the bucket index identify the key inside
+// its bucket, and the original key can be recovered for per-binding outputs.
+constexpr uint32_t inv32(uint32_t c) {
+  uint32_t x = c;
+  for (int i = 0; i < 5; ++i) x *= 2u - c * x;
+  return x;
+}
+constexpr uint64_t inv64(uint64_t c) {
+  uint64_t x = c;
+  for (int i = 0; i < 6; ++i) x *= 2ull - c * x;
+  return x;
+}
+constexpr uint32_t M32A = 0x85ebca6bu, M32B = 0xc2b2ae35u;
+constexpr uint64_t M64A = 0xff51afd7ed558ccdull, M64B = 0xc4ceb9fe1a85ec53ull;
+constexpr uint32_t I32A = inv32(M32A), I32B = inv32(M32B);
+constexpr uint64_t I64A = inv64(M64A), I64B = inv64(M64B);
+static_assert(M32A * I32A == 1u && M32B * I32B == 1u, "32-bit inverses");
+static_assert(M64A * I64A == 1ull && M64B * I64B == 1ull, "64-bit inverses");
+
+__host__ __device__ __forceinline__ uint32_t mix32(uint32_t h) {
+  h ^= h >> 16; h *= M32A; h ^= h >> 13; h *= M32B; h ^= h >> 16;
+  return h;
+}
+__host__ __device__ __forceinline__ uint32_t unmix32(uint32_t h) {
+  h ^= h >> 16; h *= I32B; h ^= (h >> 13) ^ (h >> 26); h *= I32A; h ^= h >> 16;
+  return h;
+}
+__host__ __device__ __forceinline__ uint64_t mix64(uint64_t h) {
+  h ^= h >> 33; h *= M64A; h ^= h >> 33; h *= M64B; h ^= h >> 33;
+  return h;
+}
+__host__ __device__ __forceinline__ uint64_t unmix64(uint64_t h) {
+  h ^= h >> 33; h *= I64B; h ^= h >> 33; h *= I64A; h ^= h >> 33;
+  return h;
+}
+
+// ------------------------------------------------------------------ record formats
+// A record is a key-grouped event: the letter (predicate byte) in the low 8
+// bits and, above it, the part of the mixed key not implied by the bucket.
+enum Fmt {
+  FMT_K32 = 0,   // one variable, 32-bit key: u32 record = low (32-B1) mixed bits << 8 | letter
+  FMT_K64 = 1,   // one variable, 64-bit key: u64 record = low (64-B1) mixed bits << 8 | letter
+  FMT_K2 = 2     // two variables, key (d0 << 32) | d1: u64 record = low (32-B1) bits of mix32(d0) << 40 | d1 << 8 | letter
+};
+
+template <int F> struct RecT { typedef uint64_t type; };
+template <> struct RecT<FMT_K32> { typedef uint32_t type; };
+
+struct Bucketed {
+  uint32_t bucket;   // first-level bucket
+  uint64_t rec;
+};
+
+template <int F>
+__device__ __forceinline__ Bucketed make_record(uint64_t key, uint32_t letter, int B1, int nq) {
+  Bucketed r;
+  if (F == FMT_K32) {
+    uint32_t h = nq == 0 ? 0u : mix32((uint32_t)key);
+    r.bucket = h >> (32 - B1);
+    r.rec = ((uint64_t)(h & (0xFFFFFFFFu >> B1)) << 8) | letter;
+  } else if (F == FMT_K64) {
+    uint64_t h = mix64(key);
+    r.bucket = (uint32_t)(h >> (64 - B1));
+    r.rec = ((h & (~0ull >> B1)) << 8) | letter;
+  } else {
+    uint32_t h = mix32((uint32_t)(key >> 32));
+    r.bucket = h >> (32 - B1);
+    r.rec = ((uint64_t)(h & (0xFFFFFFFFu >> B1)) << 40) | ((key & 0xFFFFFFFFull) << 8) | letter;
+  }
+  return r;
+}
+
+// bit position of the second-level split inside a record (top B2 bits of the
+// local part of the mixed outer key)
+template <int F>
+__host__ __device__ __forceinline__ int sub_shift(int B1, int B2) {
+  if (F == FMT_K32) return 8 + (32 - B1 - B2);
+  if (F == FMT_K64) return 8 + (64 - B1 - B2);
+  return 40 + (32 - B1 - B2);
+}
+
+// original binding key of a slot key (record >> 8) in first-level bucket b1
+template <int F>
+__device__ __forceinline__ uint64_t original_key(uint64_t slot_key, uint32_t b1, int B1, int nq) {
+  if (F == FMT_K32) {
+    if (nq == 0) return 0;
+    return unmix32((b1 << (32 - B1)) | (uint32_t)slot_key);
+  }
+  if (F == FMT_K64) return unmix64(((uint64_t)b1 << (64 - B1)) | slot_key);
+  uint32_t u = unmix32((b1 << (32 - B1)) | (uint32_t)(slot_key >> 32));
+  return ((uint64_t)u << 32) | (slot_key & 0xFFFFFFFFull);
+}
+template <int F>
+__device__ __forceinline__ uint32_t original_outer(uint32_t u_local, uint32_t b1, int B1) {
+  return unmix32((b1 << (32 - B1)) | u_local);
+}
+
+// ------------------------------------------------------------------ transition maps
+// A map is 16 nibbles: nibble s = target state of s.  apply(M, m) is "M then m":
+// result nibble s = m[M[s]].
+constexpr uint64_t IDENTITY_MAP = 0xFEDCBA9876543210ull;
+
+__device__ __forceinline__ uint64_t apply_map(uint64_t M, uint64_t m, int n_states) {
+  uint64_t r = IDENTITY_MAP;
+#pragma unroll 4
+  for (int s = 0; s < n_states; ++s) {
+    uint64_t q = (M >> (4 * s)) & 15ull;
+    uint64_t t = (m >> (4 * q)) & 15ull;
+    r = (r & ~(15ull << (4 * s))) | (t << (4 * s));
+  }
+  return r;
+}
+
+__device__ __forceinline__ uint32_t step_state(uint32_t q, uint64_t m) {
+  return (uint32_t)((m >> (4 * q)) & 15ull);
+}
+
+// ------------------------------------------------------------------ monitor and formula tables
+struct MonitorTab {
+  uint64_t maps[RV_MAX_LETTERS];
+  uint8_t labels[RV_MAX_STATES];
+  int n_states;
+  int q0;
+  int n_letters;
+  int nq;
+  rv_quant q[2];
+};
+
+// ------------------------------------------------------------------ accumulators of one verification
+enum {
+  ERR_LETTER = 1,       // predicate byte out of range
+  ERR_TS = 2,           // timestamps decrease
+  ERR_OUTER_FULL = 4,   // too many outer bindings in one bucket
+  ERR_SPIN = 8,         // a bounded wait gave up
+  ERR_POOL = 16         // pair pool exhausted
+};
+
+struct Acc {
+  unsigned long long level_counts[2][6];
+  unsigned long long n_nodes[2];
+  unsigned long long n_out, n_out_outer;
+  unsigned int err;
+  unsigned int n_units;
+  unsigned int n_tiles2;
+  unsigned int n_groups[8];
+  unsigned long long pair_top[2];
+};
+
+}  // namespace rvd

@@ -1,0 +1,278 @@
+"""Thin ctypes binding of librv (include/rv.h): argument marshalling only.
+
+Every step of verification runs inside librv's CUDA kernels; this module only
+converts Python/NumPy/PyTorch arguments into the C structs and back.  PyTorch
+provides device memory (workspaces, outputs) and streams.  The library must
+be built (``python -m paper_1411_2239_b300.build``); loading fails loudly
+otherwise -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librv.so")
+
+RV_OK, RV_EPARSE, RV_EUNSUPPORTED, RV_EINVAL, RV_ENOMEM, RV_EAGAIN, RV_ETIMEOUT, RV_ECUDA, RV_EINTERNAL = range(9)
+STATUS_NAMES = ["RV_OK", "RV_EPARSE", "RV_EUNSUPPORTED", "RV_EINVAL", "RV_ENOMEM", "RV_EAGAIN",
+                "RV_ETIMEOUT", "RV_ECUDA", "RV_EINTERNAL"]
+ONEHOT, BITMASK = 0, 1
+Q_A, Q_E = 0, 1
+OPS = {"<": 0, "<=": 1, ">": 2, ">=": 3, "=": 4}
+VERDICT_NAMES = ["F", "Fc", "Fp", "Tp", "Tc", "T"]
+
+
+class RVError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {msg}")
+        self.status = status
+
+
+class _Schema(ctypes.Structure):
+    _fields_ = [("n_codes", ctypes.c_int), ("code_names", ctypes.POINTER(ctypes.c_char_p)),
+                ("alphabet", ctypes.c_int), ("key_bits", ctypes.c_int)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int) for n in ("n_quant", "n_states", "n_letters", "q0", "key_bits", "alphabet")]
+
+
+class _Trace(ctypes.Structure):
+    _fields_ = [("key", ctypes.c_void_p), ("pred", ctypes.c_void_p), ("ts", ctypes.c_void_p), ("n", ctypes.c_uint64)]
+
+
+class _Result(ctypes.Structure):
+    _fields_ = [("root", ctypes.c_int32), ("status", ctypes.c_int32), ("root_counts", ctypes.c_uint64 * 6),
+                ("level_counts", (ctypes.c_uint64 * 6) * 2), ("n_nodes", ctypes.c_uint64 * 2),
+                ("events", ctypes.c_uint64)]
+
+
+class _Bindings(ctypes.Structure):
+    _fields_ = [("keys", ctypes.c_void_p), ("verdicts", ctypes.c_void_p), ("capacity", ctypes.c_uint64),
+                ("outer_keys", ctypes.c_void_p), ("outer_verdicts", ctypes.c_void_p),
+                ("outer_capacity", ctypes.c_uint64)]
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("bucket_bits", ctypes.c_int), ("sub_bucket_bits", ctypes.c_int), ("unit_records", ctypes.c_int)]
+
+
+RESULT_BYTES = ctypes.sizeof(_Result)
+_lib = None
+
+
+def lib():
+    """Load librv.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"librv.so not built at {LIB_PATH}; run python -m paper_1411_2239_b300.build")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, u64, i32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int
+        L.rv_compile_formula.argtypes = [ctypes.c_char_p, ctypes.POINTER(_Schema), ctypes.POINTER(vp),
+                                         ctypes.c_char_p, ctypes.c_size_t]
+        L.rv_formula_get_info.argtypes = [vp, ctypes.POINTER(_Info)]
+        L.rv_formula_tables.argtypes = [vp, ctypes.POINTER(u64), i32, ctypes.POINTER(ctypes.c_uint8)]
+        L.rv_formula_quantifier.argtypes = [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                            ctypes.POINTER(u64), ctypes.POINTER(u64)]
+        L.rv_formula_free.argtypes = [vp]
+        L.rv_formula_free.restype = None
+        L.rv_valuate.argtypes = [i32, i32, u64, u64, ctypes.POINTER(u64), ctypes.POINTER(i32)]
+        L.rv_verify_workspace_size.argtypes = [vp, u64, i32, ctypes.POINTER(_Opts)]
+        L.rv_verify_workspace_size.restype = ctypes.c_size_t
+        L.rv_verify_trace.argtypes = [vp, ctypes.POINTER(_Trace), i32, vp, ctypes.c_size_t, ctypes.POINTER(_Result),
+                                      ctypes.POINTER(_Bindings), ctypes.POINTER(_Opts), vp]
+        L.rv_verify_trace_async.argtypes = [vp, ctypes.POINTER(_Trace), vp, ctypes.c_size_t, vp,
+                                            ctypes.POINTER(_Bindings), ctypes.POINTER(_Opts), vp]
+        L.rv_last_error.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    return lib().rv_last_error().decode()
+
+
+def _check(st):
+    if st != RV_OK:
+        raise RVError(st, last_error())
+
+
+@dataclass
+class Quantifier:
+    kind: int
+    op: int
+    num: int
+    den: int
+
+
+class Formula:
+    """A compiled LTL4-C formula (owns an rv_formula)."""
+
+    def __init__(self, text: str, codes, alphabet: str = "onehot", key_bits: int = 32):
+        L = lib()
+        self.text, self.codes = text, list(codes)
+        self.alphabet = ONEHOT if alphabet == "onehot" else BITMASK
+        names = (ctypes.c_char_p * len(self.codes))(*[c.encode() for c in self.codes])
+        self._names = names
+        sch = _Schema(len(self.codes), names, self.alphabet, key_bits)
+        h = ctypes.c_void_p()
+        err = ctypes.create_string_buffer(512)
+        st = L.rv_compile_formula(text.encode(), ctypes.byref(sch), ctypes.byref(h), err, 512)
+        if st != RV_OK:
+            raise RVError(st, err.value.decode())
+        self._h = h
+        info = _Info()
+        _check(L.rv_formula_get_info(h, ctypes.byref(info)))
+        self.n_quant, self.n_states, self.n_letters = info.n_quant, info.n_states, info.n_letters
+        self.q0, self.key_bits = info.q0, info.key_bits
+
+    @property
+    def handle(self):
+        return self._h
+
+    def tables(self):
+        maps = (ctypes.c_uint64 * self.n_letters)()
+        labels = (ctypes.c_uint8 * 16)()
+        _check(lib().rv_formula_tables(self._h, maps, self.n_letters, labels))
+        return [int(m) for m in maps], [int(x) for x in labels]
+
+    def quantifier(self, level):
+        k, o = ctypes.c_int(), ctypes.c_int()
+        n, d = ctypes.c_uint64(), ctypes.c_uint64()
+        _check(lib().rv_formula_quantifier(self._h, level, ctypes.byref(k), ctypes.byref(o), ctypes.byref(n),
+                                           ctypes.byref(d)))
+        return Quantifier(k.value, o.value, n.value, d.value)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.rv_formula_free(h)
+            self._h = None
+
+
+def valuate(kind, op, num, den, v) -> int:
+    arr = (ctypes.c_uint64 * 6)(*[int(x) for x in v])
+    out = ctypes.c_int()
+    _check(lib().rv_valuate(kind, op, num, den, arr, ctypes.byref(out)))
+    return out.value
+
+
+@dataclass
+class Result:
+    root: int
+    status: int
+    root_counts: list
+    level_counts: list
+    n_nodes: list
+    events: int
+    bindings: dict = field(default_factory=dict)
+    outer: dict = field(default_factory=dict)
+
+
+def _result(r: _Result) -> Result:
+    return Result(r.root, r.status, list(r.root_counts), [list(r.level_counts[0]), list(r.level_counts[1])],
+                  list(r.n_nodes), r.events)
+
+
+def _opts(opts):
+    if not opts:
+        return None
+    return ctypes.byref(_Opts(opts.get("bucket_bits", 0), opts.get("sub_bucket_bits", 0), opts.get("unit_records", 0)))
+
+
+def workspace_size(formula: Formula, n: int, host_input: bool = False, opts=None) -> int:
+    return int(lib().rv_verify_workspace_size(formula.handle, n, int(host_input), _opts(opts)))
+
+
+_ws_cache = {}
+
+
+def workspace(nbytes: int, device="cuda"):
+    """A cached torch uint8 device buffer of at least nbytes."""
+    import torch
+    buf = _ws_cache.get(device)
+    if buf is None or buf.numel() < nbytes:
+        _ws_cache.pop(device, None)
+        buf = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=device)
+        _ws_cache[device] = buf
+    return buf
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return x.data_ptr()
+
+
+def _stream_handle(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def verify(formula: Formula, key, pred, ts=None, stream=None, want_bindings=False, opts=None, ws=None) -> Result:
+    """Verify one trace.  key/pred/ts: torch CUDA tensors (device path) or
+    NumPy arrays (host path: copied in by the library)."""
+    import torch
+    on_device = isinstance(pred, torch.Tensor) and pred.is_cuda
+    if not on_device:
+        key = np.ascontiguousarray(key)
+        pred = np.ascontiguousarray(pred, dtype=np.uint8)
+        ts = None if ts is None else np.ascontiguousarray(ts, dtype=np.uint32)
+        want_kb = 8 if formula.key_bits == 64 else 4
+        if key.dtype.itemsize != want_kb:
+            key = key.astype(np.uint64 if want_kb == 8 else np.uint32)
+    n = int(pred.shape[0])
+    tr = _Trace(_ptr(key), _ptr(pred), _ptr(ts), n)
+    need = workspace_size(formula, n, not on_device, opts)
+    if ws is None:
+        ws = workspace(need)
+    binds = None
+    outs = {}
+    if want_bindings:
+        cap = max(n, 1)
+        outs = {"keys": torch.empty(cap, dtype=torch.int64, device="cuda"),
+                "verdicts": torch.empty(cap, dtype=torch.uint8, device="cuda"),
+                "okeys": torch.empty(cap, dtype=torch.int64, device="cuda"),
+                "overdicts": torch.empty(cap, dtype=torch.uint8, device="cuda")}
+        binds = ctypes.byref(_Bindings(outs["keys"].data_ptr(), outs["verdicts"].data_ptr(), cap,
+                                       outs["okeys"].data_ptr(), outs["overdicts"].data_ptr(), cap))
+    r = _Result()
+    _check(lib().rv_verify_trace(formula.handle, ctypes.byref(tr), int(on_device), ctypes.c_void_p(ws.data_ptr()),
+                                 ws.numel(), ctypes.byref(r), binds, _opts(opts), _stream_handle(stream)))
+    res = _result(r)
+    if want_bindings:
+        if formula.n_quant == 2:
+            ni, no = int(res.n_nodes[1]), int(res.n_nodes[0])
+        else:
+            ni, no = int(res.n_nodes[0]), 0
+        k = outs["keys"][:ni].cpu().numpy().view(np.uint64)
+        v = outs["verdicts"][:ni].cpu().numpy()
+        res.bindings = dict(zip(k.tolist(), v.tolist()))
+        if no:
+            k = outs["okeys"][:no].cpu().numpy().view(np.uint64)
+            v = outs["overdicts"][:no].cpu().numpy()
+            res.outer = dict(zip(k.tolist(), v.tolist()))
+    return res
+
+
+def verify_async(formula: Formula, key, pred, ws, dev_result, stream=None, opts=None, ts=None):
+    """Enqueue verification of a device-resident trace; the result lands in
+    dev_result (a torch uint8 CUDA tensor of RESULT_BYTES bytes)."""
+    n = int(pred.shape[0])
+    tr = _Trace(_ptr(key), _ptr(pred), _ptr(ts), n)
+    _check(lib().rv_verify_trace_async(formula.handle, ctypes.byref(tr), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                       ctypes.c_void_p(dev_result.data_ptr()), None, _opts(opts),
+                                       _stream_handle(stream)))
+
+
+def parse_result(raw: bytes) -> Result:
+    r = _Result.from_buffer_copy(raw)
+    return _result(r)
