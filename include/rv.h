@@ -148,7 +148,7 @@ typedef struct {
 /* Tuning knobs; zero means "choose automatically". */
 typedef struct {
   int bucket_bits;       /* log2 of the first-level key buckets, 8..11 */
-  int sub_bucket_bits;   /* log2 of the second-level split, 0..6 */
+  int sub_bucket_bits;   /* log2 of the second-level split, 0..7 */
   int unit_records;      /* records folded by one CTA, multiple of 256 */
 } rv_verify_opts;
 

@@ -13,7 +13,7 @@
 //          Warps take contiguous slices of the unit; each key (binding) gets a
 //          slot in a shared-memory hash table and every warp composes the
 //          64-bit transition maps of its slice's letters per slot (equal keys
-//          inside a 32-record round are grouped with __match_any_sync and
+//          inside a 32-record round are grouped by a ballot match and
 //          applied in lane order).  The warps' maps are then composed in
 //          order.  This is the per-cluster monitor of ProcessBuffer, with
 //          the long clusters of a Zipf head split across warps and CTAs and
@@ -53,6 +53,8 @@ constexpr uint16_t FULL_SLOT = 0xFFFE;
 constexpr uint64_t EMPTY_KEY = ~0ull;
 constexpr unsigned FULL = 0xFFFFFFFFu;
 constexpr int SPIN_LIMIT = 1 << 22;
+constexpr int BATCH = 16;      // rounds of 32 events whose loads are issued together
+constexpr int FBATCH = 8;      // the same for the fold
 
 struct Tile { uint32_t bucket, k, K, pad; uint64_t begin, end; };
 struct Item { uint64_t off; uint32_t cnt, pad; };
@@ -62,6 +64,20 @@ struct Pair { uint64_t key, map; };
 __device__ __forceinline__ uint32_t lanemask_lt() {
   uint32_t m;
   asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// Lanes of the warp whose `valid` flag and low BITS bits of v equal this
+// lane's: one ballot per bit (full rate).
+template <int BITS>
+__device__ __forceinline__ uint32_t match_bits(uint32_t v, bool valid) {
+  const uint32_t vb = __ballot_sync(FULL, valid);
+  uint32_t m = valid ? vb : ~vb;
+#pragma unroll
+  for (int k = 0; k < BITS; ++k) {
+    const uint32_t bk = __ballot_sync(FULL, (v >> k) & 1u);
+    m &= ((v >> k) & 1u) ? bk : ~bk;
+  }
   return m;
 }
 
@@ -86,17 +102,25 @@ k_hist(const void* keyp, const uint32_t* ts, uint64_t n, uint64_t per_warp, int 
   if (gw >= G_w) return;
   const uint64_t begin = (uint64_t)gw * per_warp, end = min(n, begin + per_warp);
   bool bad_ts = false;
-  for (uint64_t base = begin; base < end; base += 32) {
-    const uint64_t i = base + lane;
-    const bool v = i < end;
-    uint32_t b = 0xFFFFFFFFu;
-    if (v) {
-      b = make_record<F>(load_key<F>(keyp, i), 0, B1, nq).bucket;
-      if (ts && i > 0 && ts[i] < ts[i - 1]) bad_ts = true;
+  // BATCH rounds of 32 events: all loads of a batch are in flight together
+  for (uint64_t base = begin; base < end; base += 32 * BATCH) {
+    uint32_t b[BATCH];
+#pragma unroll
+    for (int j = 0; j < BATCH; ++j) {
+      const uint64_t i = base + j * 32 + lane;
+      b[j] = i < end ? make_record<F>(load_key<F>(keyp, i), 0, B1, nq).bucket : 0xFFFFFFFFu;
     }
-    const uint32_t peers = __match_any_sync(FULL, b);
-    if (v && lane == __ffs(peers) - 1) cnt[b] += __popc(peers);
-    __syncwarp();
+    if (ts) {
+#pragma unroll
+      for (int j = 0; j < BATCH; ++j) {
+        const uint64_t i = base + j * 32 + lane;
+        if (i < end && i > 0 && ts[i] < ts[i - 1]) bad_ts = true;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < BATCH; ++j) {
+      if (b[j] != 0xFFFFFFFFu) atomicAdd(&cnt[b[j]], 1u);
+    }
   }
   if (__any_sync(FULL, bad_ts) && lane == 0) atomicOr(&acc->err, ERR_TS);
   for (int b = lane; b < P; b += 32) hist[(uint64_t)gw * P + b] = cnt[b];
@@ -188,25 +212,33 @@ k_scatter(const void* keyp, const uint8_t* pred, uint64_t n, uint64_t per_warp, 
   const uint64_t begin = (uint64_t)gw * per_warp, end = min(n, begin + per_warp);
   bool bad = false;
   const uint32_t lt = lanemask_lt();
-  for (uint64_t base = begin; base < end; base += 32) {
-    const uint64_t i = base + lane;
-    const bool v = i < end;
-    uint32_t b = 0xFFFFFFFFu;
-    Rec rec = 0;
-    if (v) {
-      uint32_t letter = pred[i];
-      if (letter >= (uint32_t)n_letters) { bad = true; letter = 0; }
-      Bucketed r = make_record<F>(load_key<F>(keyp, i), letter, B1, nq);
-      b = r.bucket;
-      rec = (Rec)r.rec;
+  for (uint64_t base = begin; base < end; base += 32 * BATCH) {
+    uint32_t b[BATCH];
+    Rec rec[BATCH];
+#pragma unroll
+    for (int j = 0; j < BATCH; ++j) {
+      const uint64_t i = base + j * 32 + lane;
+      b[j] = 0xFFFFFFFFu;
+      rec[j] = 0;
+      if (i < end) {
+        uint32_t letter = pred[i];
+        if (letter >= (uint32_t)n_letters) { bad = true; letter = 0; }
+        Bucketed r = make_record<F>(load_key<F>(keyp, i), letter, B1, nq);
+        b[j] = r.bucket;
+        rec[j] = (Rec)r.rec;
+      }
     }
-    const uint32_t peers = __match_any_sync(FULL, b);
-    uint32_t pos = 0;
-    if (v) pos = cur[b] + __popc(peers & lt);
-    __syncwarp();
-    if (v && lane == __ffs(peers) - 1) cur[b] += __popc(peers);
-    __syncwarp();
-    if (v) out[pos] = rec;
+#pragma unroll
+    for (int j = 0; j < BATCH; ++j) {
+      const bool v = b[j] != 0xFFFFFFFFu;
+      const uint32_t peers = match_bits<11>(b[j], v);
+      uint32_t pos = 0;
+      if (v) pos = cur[b[j]] + __popc(peers & lt);
+      __syncwarp();
+      if (v && lane == __ffs(peers) - 1) cur[b[j]] += __popc(peers);
+      __syncwarp();
+      if (v) out[pos] = rec[j];
+    }
   }
   if (__any_sync(FULL, bad) && lane == 0) atomicOr(&acc->err, ERR_LETTER);
 }
@@ -266,7 +298,7 @@ template <int F>
 __global__ void __launch_bounds__(SC_WARPS * 32)
 k_hist2(const typename RecT<F>::type* recs, const Tile* tiles, const unsigned int* n_tiles, int B1, int B2,
         uint32_t* hist2) {
-  __shared__ uint32_t cnt_all[SC_WARPS][64];
+  __shared__ uint32_t cnt_all[SC_WARPS][128];
   const int P2 = 1 << B2;
   const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t tile = blockIdx.x * SC_WARPS + wl;
@@ -281,7 +313,7 @@ k_hist2(const typename RecT<F>::type* recs, const Tile* tiles, const unsigned in
     const bool v = i < tl.end;
     uint32_t b = 0xFFFFFFFFu;
     if (v) b = (uint32_t)((uint64_t)recs[i] >> sh) & (P2 - 1);
-    const uint32_t peers = __match_any_sync(FULL, b);
+    const uint32_t peers = match_bits<7>(b, v);
     if (v && lane == __ffs(peers) - 1) cnt[b] += __popc(peers);
     __syncwarp();
   }
@@ -308,7 +340,7 @@ template <int F>
 __global__ void __launch_bounds__(SC_WARPS * 32)
 k_scatter2(const typename RecT<F>::type* in, const Tile* tiles, const unsigned int* n_tiles, int B1, int B2,
            const uint32_t* pre2, const uint64_t* bstart2, typename RecT<F>::type* out) {
-  __shared__ uint32_t cur_all[SC_WARPS][64];
+  __shared__ uint32_t cur_all[SC_WARPS][128];
   const int P2 = 1 << B2;
   const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t tile = blockIdx.x * SC_WARPS + wl;
@@ -326,7 +358,7 @@ k_scatter2(const typename RecT<F>::type* in, const Tile* tiles, const unsigned i
     uint32_t b = 0xFFFFFFFFu;
     typename RecT<F>::type rec = 0;
     if (v) { rec = in[i]; b = (uint32_t)((uint64_t)rec >> sh) & (P2 - 1); }
-    const uint32_t peers = __match_any_sync(FULL, b);
+    const uint32_t peers = match_bits<7>(b, v);
     uint32_t pos = 0;
     if (v) pos = cur[b] + __popc(peers & lt);
     __syncwarp();
@@ -352,9 +384,9 @@ struct OuterTable {
   unsigned int ovf;
 };
 
-struct FinalCtx {
-  unsigned long long h0[6], h1[6];
-  unsigned long long nodes0, nodes1;
+struct FinalCtx {              // per-thread tallies, reduced once per CTA
+  uint32_t h0[6], h1[6];
+  uint32_t nodes0, nodes1;
 };
 
 struct Params {
@@ -458,11 +490,11 @@ __device__ __forceinline__ void finalize_slot(const Params& p, FinalCtx& fc, Out
   const uint32_t v = p.tab.labels[state];
   const uint32_t b1 = bucket >> p.B2;
   if (p.nq <= 1) {
-    atomicAdd(&fc.h0[v], 1ull);
-    atomicAdd(&fc.nodes0, 1ull);
+    fc.h0[v] += 1;
+    fc.nodes0 += 1;
   } else {
-    atomicAdd(&fc.h1[v], 1ull);
-    atomicAdd(&fc.nodes1, 1ull);
+    fc.h1[v] += 1;
+    fc.nodes1 += 1;
     int ui = outer_slot(U, (uint32_t)(skey >> 32));
     if (ui < 0) atomicOr(&p.acc->err, ERR_OUTER_FULL);
     else atomicAdd(&U.ucnt[ui][v], 1u);
@@ -486,8 +518,8 @@ __device__ void finalize_outer(const Params& p, FinalCtx& fc, OuterTable& U, uin
     uint64_t v6[6];
     for (int v = 0; v < 6; ++v) v6[v] = U.ucnt[i][v];
     const int vd = rvv::valuate(p.tab.q[1].kind, p.tab.q[1].op, p.tab.q[1].num, p.tab.q[1].den, v6);
-    atomicAdd(&fc.h0[vd], 1ull);
-    atomicAdd(&fc.nodes0, 1ull);
+    fc.h0[vd] += 1;
+    fc.nodes0 += 1;
     if (p.out.outer_keys) {
       unsigned long long idx = atomicAdd(&p.acc->n_out_outer, 1ull);
       if (idx < p.out.outer_capacity) {
@@ -499,14 +531,24 @@ __device__ void finalize_outer(const Params& p, FinalCtx& fc, OuterTable& U, uin
 }
 
 __device__ void flush_final(const Params& p, FinalCtx& fc) {
-  if (threadIdx.x < 6) {
-    if (fc.h0[threadIdx.x]) atomicAdd(&p.acc->level_counts[0][threadIdx.x], fc.h0[threadIdx.x]);
-    if (fc.h1[threadIdx.x]) atomicAdd(&p.acc->level_counts[1][threadIdx.x], fc.h1[threadIdx.x]);
+  uint32_t v[14];
+  for (int i = 0; i < 6; ++i) { v[i] = fc.h0[i]; v[6 + i] = fc.h1[i]; }
+  v[12] = fc.nodes0;
+  v[13] = fc.nodes1;
+  for (int i = 0; i < 14; ++i) {
+    uint32_t x = __reduce_add_sync(FULL, v[i]);
+    if ((threadIdx.x & 31) == 0 && x) {
+      unsigned long long* dst = i < 6 ? &p.acc->level_counts[0][i]
+                                : i < 12 ? &p.acc->level_counts[1][i - 6]
+                                         : &p.acc->n_nodes[i - 12];
+      atomicAdd(dst, (unsigned long long)x);
+    }
   }
-  if (threadIdx.x == 0) {
-    if (fc.nodes0) atomicAdd(&p.acc->n_nodes[0], fc.nodes0);
-    if (fc.nodes1) atomicAdd(&p.acc->n_nodes[1], fc.nodes1);
-  }
+}
+
+__device__ __forceinline__ void clear_final(FinalCtx& fc) {
+  for (int i = 0; i < 6; ++i) { fc.h0[i] = 0; fc.h1[i] = 0; }
+  fc.nodes0 = fc.nodes1 = 0;
 }
 
 // ------------------------------------------------------------------ fold
@@ -515,8 +557,6 @@ struct FoldShared {
   uint64_t wmap[FOLD_WARPS][SLOTS];
   SlotTable T;
   OuterTable U;
-  FinalCtx fc;
-  uint8_t stage[FOLD_WARPS][32];
   uint32_t pass_bits[64], pass_val[64];
   int npass;
   uint64_t item_off;
@@ -531,11 +571,18 @@ k_fold(const typename RecT<F>::type* recs, const Tile* units, const unsigned int
   FoldShared& S = *reinterpret_cast<FoldShared*>(fold_smem);
   const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ns = p.tab.n_states;
+  const uint32_t lt = lanemask_lt();
   for (int i = threadIdx.x; i < RV_MAX_LETTERS; i += blockDim.x) S.lmap[i] = p.tab.maps[i];
-  if (threadIdx.x < 6) { S.fc.h0[threadIdx.x] = 0; S.fc.h1[threadIdx.x] = 0; }
-  if (threadIdx.x == 0) { S.fc.nodes0 = 0; S.fc.nodes1 = 0; }
+  FinalCtx fc;
+  clear_final(fc);
+  __shared__ unsigned int s_next;
   const unsigned int nun = *n_units;
-  for (unsigned int u = blockIdx.x; u < nun; u += gridDim.x) {
+  while (true) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_next = atomicAdd(&p.acc->next_unit, 1u);
+    __syncthreads();
+    const unsigned int u = s_next;
+    if (u >= nun) break;
     const Tile t = units[u];
     const bool single = t.K == 1;
     const uint64_t len = t.end - t.begin;
@@ -556,31 +603,48 @@ k_fold(const typename RecT<F>::type* recs, const Tile* units, const unsigned int
       const uint32_t val = S.pass_val[S.npass - 1];
       reset_table(S.T);
       __syncthreads();
-      for (uint64_t base = wbeg; base < wend; base += 32) {
-        const uint64_t i = base + lane;
-        const bool v = i < wend;
-        uint64_t rec = v ? (uint64_t)recs[i] : 0;
-        const uint64_t key = rec >> 8;
-        int slot = -1;
-        if (v && in_pass(key, bits, val)) {
-          slot = find_or_insert(S.T, key, p.acc, [&](unsigned int s) {
-            for (int w = 0; w < FOLD_WARPS; ++w) S.wmap[w][s] = IDENTITY_MAP;
-          });
+      for (uint64_t base0 = wbeg; base0 < wend; base0 += 32 * FBATCH) {
+        uint64_t rb[FBATCH];
+#pragma unroll
+        for (int j = 0; j < FBATCH; ++j) {
+          const uint64_t i = base0 + j * 32 + lane;
+          rb[j] = i < wend ? (uint64_t)recs[i] : 0;
         }
-        const uint32_t peers = __match_any_sync(FULL, slot);
-        S.stage[wl][lane] = (uint8_t)(rec & 0xFF);
-        __syncwarp();
-        if (slot >= 0 && lane == __ffs(peers) - 1) {
-          uint64_t M = S.wmap[wl][slot];
-          uint32_t m = peers;
-          while (m) {
-            const int j = __ffs(m) - 1;
-            m &= m - 1;
-            M = apply_map(M, S.lmap[S.stage[wl][j]], ns);
+#pragma unroll
+        for (int j = 0; j < FBATCH; ++j) {
+          const uint64_t rec = rb[j];
+          const bool v = base0 + j * 32 + lane < wend;
+          const uint64_t key = rec >> 8;
+          int slot = -1;
+          if (v && in_pass(key, bits, val)) {
+            slot = find_or_insert(S.T, key, p.acc, [&](unsigned int s) {
+              for (int w = 0; w < FOLD_WARPS; ++w) S.wmap[w][s] = IDENTITY_MAP;
+            });
           }
-          S.wmap[wl][slot] = M;
+          // ordered composition of the letters of equal slots in this round:
+          // a tree over ranks inside each group (rank r absorbs rank r+s)
+          const bool valid = slot >= 0;
+          const uint32_t peers = match_bits<10>((uint32_t)slot, valid);
+          const int r = __popc(peers & lt), g = __popc(peers);
+          uint64_t M = valid ? S.lmap[rec & 0xFF] : IDENTITY_MAP;
+          const unsigned gmax = __reduce_max_sync(FULL, valid ? (unsigned)g : 1u);
+          // nxt: lane of rank r + st in my group (pointer doubling), -1 if none
+          int nxt = -1;
+          if (gmax > 1 && valid) {
+            const uint32_t above = peers & ~((2u << lane) - 1u);
+            nxt = above ? __ffs(above) - 1 : -1;
+          }
+          for (int st = 1; st < (int)gmax; st <<= 1) {
+            const bool take = valid && (r & (2 * st - 1)) == 0 && nxt >= 0;
+            const int src = nxt >= 0 ? nxt : lane;
+            const uint64_t o = __shfl_sync(FULL, M, src);
+            const int n2 = __shfl_sync(FULL, nxt, src);
+            if (take) M = apply_map(M, o, ns);
+            nxt = nxt >= 0 ? n2 : -1;
+          }
+          if (valid && r == 0) S.wmap[wl][slot] = apply_map(S.wmap[wl][slot], M, ns);
+          __syncwarp();
         }
-        __syncwarp();
       }
       __syncthreads();
       if (S.T.ovf) {
@@ -603,18 +667,18 @@ k_fold(const typename RecT<F>::type* recs, const Tile* units, const unsigned int
       for (unsigned int s = threadIdx.x; s < nsl; s += blockDim.x) {
         uint64_t M = S.wmap[0][s];
         for (int w = 1; w < FOLD_WARPS; ++w) M = apply_map(M, S.wmap[w][s], ns);
-        if (single) finalize_slot<F>(p, S.fc, S.U, S.T.skey[s], M, t.bucket);
+        if (single) finalize_slot<F>(p, fc, S.U, S.T.skey[s], M, t.bucket);
         else pool[S.item_off + S.item_cnt + s] = Pair{S.T.skey[s], M};
       }
       __syncthreads();
       if (threadIdx.x == 0) { S.item_cnt += nsl; S.npass -= 1; }
     }
     __syncthreads();
-    if (single) finalize_outer<F>(p, S.fc, S.U, t.bucket);
+    if (single) finalize_outer<F>(p, fc, S.U, t.bucket);
     else if (threadIdx.x == 0) items[u] = Item{S.item_off, S.item_cnt, 0};
   }
   __syncthreads();
-  flush_final(p, S.fc);
+  flush_final(p, fc);
 }
 
 // Single CTA: groups of up to GC consecutive items of every bucket still
@@ -669,7 +733,6 @@ struct CombineShared {
   uint64_t smap[SLOTS];
   SlotTable T;
   OuterTable U;
-  FinalCtx fc;
   uint32_t pass_bits[64], pass_val[64];
   int npass;
   uint64_t out_off;
@@ -679,14 +742,20 @@ struct CombineShared {
 template <int F>
 __global__ void __launch_bounds__(FOLD_THREADS)
 k_combine(const Item* items_in, const Pair* pool_in, const Group* groups, const unsigned int* n_groups,
-          Params p, Item* items_out, Pair* pool_out, int dst) {
+          unsigned int* next_group, Params p, Item* items_out, Pair* pool_out, int dst) {
   extern __shared__ __align__(16) unsigned char comb_smem[];
   CombineShared& S = *reinterpret_cast<CombineShared*>(comb_smem);
   const int ns = p.tab.n_states;
-  if (threadIdx.x < 6) { S.fc.h0[threadIdx.x] = 0; S.fc.h1[threadIdx.x] = 0; }
-  if (threadIdx.x == 0) { S.fc.nodes0 = 0; S.fc.nodes1 = 0; }
+  FinalCtx fc;
+  clear_final(fc);
+  __shared__ unsigned int s_next;
   const unsigned int ng = *n_groups;
-  for (unsigned int g = blockIdx.x; g < ng; g += gridDim.x) {
+  while (true) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_next = atomicAdd(next_group, 1u);
+    __syncthreads();
+    const unsigned int g = s_next;
+    if (g >= ng) break;
     const Group G = groups[g];
     const bool final_ = G.K == 1;
     __syncthreads();
@@ -733,18 +802,18 @@ k_combine(const Item* items_in, const Pair* pool_in, const Group* groups, const 
       }
       const unsigned int nsl = min(S.T.nslots, (unsigned int)SLOTS);
       for (unsigned int s = threadIdx.x; s < nsl; s += blockDim.x) {
-        if (final_) finalize_slot<F>(p, S.fc, S.U, S.T.skey[s], S.smap[s], G.bucket);
+        if (final_) finalize_slot<F>(p, fc, S.U, S.T.skey[s], S.smap[s], G.bucket);
         else pool_out[S.out_off + S.out_cnt + s] = Pair{S.T.skey[s], S.smap[s]};
       }
       __syncthreads();
       if (threadIdx.x == 0) { S.out_cnt += nsl; S.npass -= 1; }
     }
     __syncthreads();
-    if (final_) finalize_outer<F>(p, S.fc, S.U, G.bucket);
+    if (final_) finalize_outer<F>(p, fc, S.U, G.bucket);
     else if (threadIdx.x == 0) items_out[g] = Item{S.out_off, S.out_cnt, 0};
   }
   __syncthreads();
-  flush_final(p, S.fc);
+  flush_final(p, fc);
 }
 
 __global__ void k_root(const Acc* acc, Params p, uint64_t n, rv_result* out) {
@@ -802,22 +871,18 @@ static Plan make_plan(const rv_formula* f, uint64_t n, int host_input, const rv_
   Plan pl{};
   pl.n = n;
   pl.F = f->n_quant == 2 ? FMT_K2 : (f->key_bits == 64 && f->n_quant == 1 ? FMT_K64 : FMT_K32);
-  int b1 = o && o->bucket_bits ? o->bucket_bits : 0;
-  if (!b1) {
-    b1 = 8;
-    while (b1 < 11 && (n >> b1) > 32768) ++b1;
-  }
+  // default: 256 first-level buckets (few open write frontiers in the
+  // scatter) and a second-level split down to about 8192 records per bucket
+  int b1 = o && o->bucket_bits ? o->bucket_bits : 8;
   pl.B1 = std::min(11, std::max(8, b1));
   pl.P1 = 1 << pl.B1;
-  int b2 = o && o->sub_bucket_bits >= 0 ? o->sub_bucket_bits : 0;
-  if (!(o && o->sub_bucket_bits) && f->n_quant == 2) {
-    b2 = 0;
-    while (b2 < 6 && (n >> (pl.B1 + b2)) > 8192) ++b2;
-  }
+  int b2 = 0;
+  if (o && o->sub_bucket_bits) b2 = o->sub_bucket_bits;
+  else while (b2 < 7 && (n >> (pl.B1 + b2)) > 8192) ++b2;
   b2 += extra_b2;
-  pl.B2 = std::min(6, std::max(0, b2));
+  pl.B2 = std::min(7, std::max(0, b2));
   pl.P = pl.P1 << pl.B2;
-  pl.unit = o && o->unit_records ? (uint64_t)o->unit_records : 32768;
+  pl.unit = o && o->unit_records ? (uint64_t)o->unit_records : 8192;
   pl.unit = std::max<uint64_t>(256, pl.unit);
   const uint64_t max_w = (uint64_t)num_sms() * 3 * SC_WARPS;
   uint64_t gw = (n + 2047) / 2048;
@@ -963,7 +1028,7 @@ static rv_status launch_all(const Plan& pl, const rv_formula* f, const void* key
       RV_CU(cudaMemsetAsync(&acc->pair_top[dst], 0, sizeof(unsigned long long), s));
       RV_LAUNCH("k_make_groups", k_make_groups, 1, 1024, 0, s, fin, kin, pl.P, groups, gf[l & 1], gk[l & 1], &acc->n_groups[l]);
       const int cgrid = (int)std::min<uint64_t>(pl.max_units / GC + pl.P, (uint64_t)num_sms() * 2);
-      RV_LAUNCH("k_combine", k_combine<F>, cgrid, FOLD_THREADS, sizeof(CombineShared), s, iin, pin, groups, &acc->n_groups[l], p,
+      RV_LAUNCH("k_combine", k_combine<F>, cgrid, FOLD_THREADS, sizeof(CombineShared), s, iin, pin, groups, &acc->n_groups[l], &acc->next_group[l], p,
                                                                       iout, pout, dst);
       fin = gf[l & 1];
       kin = gk[l & 1];
@@ -1027,7 +1092,7 @@ extern "C" void rv_set_allocator(rv_alloc_fn alloc, rv_free_fn free_fn, void* ct
 extern "C" size_t rv_verify_workspace_size(const rv_formula* f, uint64_t n, int host_input, const rv_verify_opts* opts) {
   if (!f) return 0;
   size_t worst = 0;
-  for (int extra = 0; extra <= 6; extra += 2) worst = std::max(worst, make_plan(f, n, host_input, opts, extra).total);
+  for (int extra = 0; extra <= 7; extra += 2) worst = std::max(worst, make_plan(f, n, host_input, opts, extra).total);
   return worst;
 }
 
@@ -1059,7 +1124,7 @@ extern "C" rv_status rv_verify_trace(const rv_formula* f, const rv_trace* t, int
   static thread_local rv_result* pinned = nullptr;
   if (!pinned && cudaMallocHost(&pinned, sizeof(rv_result)) != cudaSuccess)
     return rv_fail(RV_ECUDA, "cannot allocate pinned result buffer");
-  for (int extra = 0; extra <= 6; extra += 2) {
+  for (int extra = 0; extra <= 7; extra += 2) {
     Plan pl = make_plan(f, t->n, !on_device, opts, extra);
     unsigned char* w = (unsigned char*)ws;
     bool owned = false;
@@ -1093,7 +1158,7 @@ extern "C" rv_status rv_verify_trace(const rv_formula* f, const rv_trace* t, int
     if (owned) rv_dev_free(w);
     if (st) return st;
     *out = *pinned;
-    if (out->status == RV_EAGAIN && f->n_quant == 2 && pl.B2 < 6 && !(opts && opts->sub_bucket_bits)) continue;
+    if (out->status == RV_EAGAIN && f->n_quant == 2 && pl.B2 < 7 && !(opts && opts->sub_bucket_bits)) continue;
     if (out->status == RV_EINVAL) return rv_fail(RV_EINVAL, "trace rejected: predicate code out of range or timestamps decreasing");
     if (out->status != RV_OK) return rv_fail((rv_status)out->status, "device status %d", out->status);
     return RV_OK;

@@ -112,15 +112,46 @@ __device__ __forceinline__ uint32_t original_outer(uint32_t u_local, uint32_t b1
 // result nibble s = m[M[s]].
 constexpr uint64_t IDENTITY_MAP = 0xFEDCBA9876543210ull;
 
+// Monitors of at most 8 states keep every target in the low word, so a map
+// is 8 nibbles there and composition is a handful of byte permutes:
+// expand the second map to bytes, select bytes by the first map's nibbles,
+// and pack the selected bytes back into nibbles.
+__device__ __forceinline__ uint32_t nibbles_to_bytes_lo(uint32_t c, uint32_t& hi4) {
+  const uint32_t l = c & 0x0F0F0F0Fu, h = (c >> 4) & 0x0F0F0F0Fu;   // [c0,c2,c4,c6] [c1,c3,c5,c7]
+  hi4 = __byte_perm(l, h, 0x7362);                                   // bytes c4 c5 c6 c7
+  return __byte_perm(l, h, 0x5140);                                  // bytes c0 c1 c2 c3
+}
+__device__ __forceinline__ uint32_t bytes_to_nibbles(uint32_t r03, uint32_t r47) {
+  const uint32_t p03 = r03 | (r03 >> 4), p47 = r47 | (r47 >> 4);
+  return __byte_perm(p03, p47, 0x6420);
+}
+__device__ __forceinline__ uint32_t compose8(uint32_t M, uint32_t C) {
+  uint32_t c47;
+  const uint32_t c03 = nibbles_to_bytes_lo(C, c47);
+  return bytes_to_nibbles(__byte_perm(c03, c47, M & 0xFFFFu), __byte_perm(c03, c47, M >> 16));
+}
+// up to 16 states: two 8-byte tables, chosen per byte by bit 3 of the index
+__device__ __forceinline__ uint32_t look4(uint32_t sel16, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3) {
+  const uint32_t s7 = sel16 & 0x7777u;
+  const uint32_t a = __byte_perm(c0, c1, s7), b = __byte_perm(c2, c3, s7);
+  const uint32_t e = __byte_perm(sel16 & 0x0F0Fu, (sel16 >> 4) & 0x0F0Fu, 0x5140);   // selector bytes
+  const uint32_t mask = ((e >> 3) & 0x01010101u) * 0xFFu;
+  return (a & ~mask) | (b & mask);
+}
+__device__ __forceinline__ uint64_t compose16(uint64_t M, uint64_t C) {
+  uint32_t c1, c3;
+  const uint32_t c0 = nibbles_to_bytes_lo((uint32_t)C, c1);
+  const uint32_t c2 = nibbles_to_bytes_lo((uint32_t)(C >> 32), c3);
+  const uint32_t Ml = (uint32_t)M, Mh = (uint32_t)(M >> 32);
+  const uint32_t lo = bytes_to_nibbles(look4(Ml & 0xFFFFu, c0, c1, c2, c3), look4(Ml >> 16, c0, c1, c2, c3));
+  const uint32_t hi = bytes_to_nibbles(look4(Mh & 0xFFFFu, c0, c1, c2, c3), look4(Mh >> 16, c0, c1, c2, c3));
+  return ((uint64_t)hi << 32) | lo;
+}
+
+// "M then m": nibble s of the result is m[M[s]]
 __device__ __forceinline__ uint64_t apply_map(uint64_t M, uint64_t m, int n_states) {
-  uint64_t r = IDENTITY_MAP;
-#pragma unroll 4
-  for (int s = 0; s < n_states; ++s) {
-    uint64_t q = (M >> (4 * s)) & 15ull;
-    uint64_t t = (m >> (4 * q)) & 15ull;
-    r = (r & ~(15ull << (4 * s))) | (t << (4 * s));
-  }
-  return r;
+  if (n_states <= 8) return (M & 0xFFFFFFFF00000000ull) | compose8((uint32_t)M, (uint32_t)m);
+  return compose16(M, m);
 }
 
 __device__ __forceinline__ uint32_t step_state(uint32_t q, uint64_t m) {
@@ -156,6 +187,8 @@ struct Acc {
   unsigned int n_tiles2;
   unsigned int n_groups[8];
   unsigned long long pair_top[2];
+  unsigned int next_unit;       // dynamic work distribution of k_fold
+  unsigned int next_group[8];   // and of each k_combine level
 };
 
 }  // namespace rvd
