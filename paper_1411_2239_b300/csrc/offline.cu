@@ -244,53 +244,77 @@ k_scatter(const void* keyp, const uint8_t* pred, uint64_t n, uint64_t per_warp, 
 }
 
 // ------------------------------------------------------------------ tiles of buckets
-// Single CTA: split every non-empty bucket b (bstart[b]..bstart[b+1]) into
-// ceil(len / tile_len) tiles; first[b]/K[b] give each bucket's tile range.
-__global__ void __launch_bounds__(1024)
-k_make_tiles(const uint64_t* bstart, int P, uint64_t tile_len, Tile* tiles, uint32_t* first, uint32_t* K,
-             unsigned int* n_tiles) {
+// Every non-empty bucket b (bstart[b]..bstart[b+1]) is split into
+// ceil(len / tile_len) tiles; first[b] / K[b] give its tile range.
+__global__ void k_count_tiles(const uint64_t* bstart, int P, uint64_t tile_len, uint32_t* K) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= P) return;
+  const uint64_t len = bstart[b + 1] - bstart[b];
+  K[b] = (uint32_t)((len + tile_len - 1) / tile_len);
+}
+
+// single CTA: exclusive scan of cnt[0..P) into first[], total into *n
+__global__ void __launch_bounds__(1024) k_scan_u32(const uint32_t* cnt, int P, uint32_t* first, unsigned int* n) {
   __shared__ uint32_t wsum[32];
-  const int t = threadIdx.x;
-  const int per = (P + 1023) / 1024;
-  const int b0 = min(P, t * per), b1 = min(P, b0 + per);
-  uint32_t s = 0;
-  for (int b = b0; b < b1; ++b) {
-    uint64_t len = bstart[b + 1] - bstart[b];
-    s += (uint32_t)((len + tile_len - 1) / tile_len);
-  }
-  uint32_t x = s;
-  const int lane = t & 31, w = t >> 5;
-  for (int o = 1; o < 32; o <<= 1) {
-    uint32_t y = __shfl_up_sync(FULL, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) wsum[w] = x;
+  __shared__ uint32_t carry;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  if (t == 0) carry = 0;
   __syncthreads();
-  if (w == 0) {
-    uint32_t z = wsum[lane];
+  for (int base = 0; base < P; base += 4096) {
+    uint32_t v[4], s = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int i = base + t * 4 + j;
+      v[j] = i < P ? cnt[i] : 0u;
+      s += v[j];
+    }
+    uint32_t x = s;
     for (int o = 1; o < 32; o <<= 1) {
-      uint32_t y = __shfl_up_sync(FULL, z, o);
-      if (lane >= o) z += y;
+      const uint32_t y = __shfl_up_sync(FULL, x, o);
+      if (lane >= o) x += y;
     }
-    wsum[lane] = z;
-  }
-  __syncthreads();
-  uint32_t run = x - s + (w ? wsum[w - 1] : 0);
-  for (int b = b0; b < b1; ++b) {
-    const uint64_t lo = bstart[b], len = bstart[b + 1] - lo;
-    const uint32_t k = (uint32_t)((len + tile_len - 1) / tile_len);
-    first[b] = run;
-    K[b] = k;
-    for (uint32_t j = 0; j < k; ++j) {
-      Tile tl;
-      tl.bucket = (uint32_t)b; tl.k = j; tl.K = k; tl.pad = 0;
-      tl.begin = lo + j * tile_len;
-      tl.end = min(lo + len, tl.begin + tile_len);
-      tiles[run + j] = tl;
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    if (w == 0) {
+      uint32_t z = wsum[lane];
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, z, o);
+        if (lane >= o) z += y;
+      }
+      wsum[lane] = z;
     }
-    run += k;
+    __syncthreads();
+    uint32_t run = carry + x - s + (w ? wsum[w - 1] : 0u);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int i = base + t * 4 + j;
+      if (i < P) first[i] = run;
+      run += v[j];
+    }
+    __syncthreads();
+    if (t == 1023) carry = run;
+    __syncthreads();
   }
-  if (t == 1023) *n_tiles = run;
+  if (t == 0) *n = carry;
+}
+
+// one thread per tile: binary search of its bucket in first[]
+__global__ void k_emit_tiles(const uint64_t* bstart, int P, uint64_t tile_len, const uint32_t* first, const uint32_t* K,
+                             const unsigned int* n_tiles, Tile* tiles) {
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= *n_tiles) return;
+  int lo = 0, hi = P - 1;            // last bucket with first[b] <= t and K[b] > 0
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (first[mid] <= t) lo = mid; else hi = mid - 1;
+  }
+  // the largest b with first[b] <= t has first[b] + K[b] = first[b+1] > t, so K[b] > 0
+  const uint32_t j = t - first[lo];
+  Tile tl;
+  tl.bucket = (uint32_t)lo; tl.k = j; tl.K = K[lo]; tl.pad = 0;
+  tl.begin = bstart[lo] + j * tile_len;
+  tl.end = min(bstart[lo + 1], tl.begin + tile_len);
+  tiles[t] = tl;
 }
 
 // ------------------------------------------------------------------ level-2 multisplit
@@ -308,15 +332,18 @@ k_hist2(const typename RecT<F>::type* recs, const Tile* tiles, const unsigned in
   __syncwarp();
   const Tile tl = tiles[tile];
   const int sh = sub_shift<F>(B1, B2);
-  for (uint64_t base = tl.begin; base < tl.end; base += 32) {
-    const uint64_t i = base + lane;
-    const bool v = i < tl.end;
-    uint32_t b = 0xFFFFFFFFu;
-    if (v) b = (uint32_t)((uint64_t)recs[i] >> sh) & (P2 - 1);
-    const uint32_t peers = match_bits<7>(b, v);
-    if (v && lane == __ffs(peers) - 1) cnt[b] += __popc(peers);
-    __syncwarp();
+  for (uint64_t base = tl.begin; base < tl.end; base += 32 * BATCH) {
+    uint32_t b[BATCH];
+#pragma unroll
+    for (int j = 0; j < BATCH; ++j) {
+      const uint64_t i = base + j * 32 + lane;
+      b[j] = i < tl.end ? (uint32_t)((uint64_t)recs[i] >> sh) & (P2 - 1) : 0xFFFFFFFFu;
+    }
+#pragma unroll
+    for (int j = 0; j < BATCH; ++j)
+      if (b[j] != 0xFFFFFFFFu) atomicAdd(&cnt[b[j]], 1u);
   }
+  __syncwarp();
   for (int b = lane; b < P2; b += 32) hist2[(uint64_t)tile * P2 + b] = cnt[b];
 }
 
@@ -328,10 +355,16 @@ __global__ void k_scan2(uint32_t* hist2, const uint32_t* tfirst, const uint32_t*
   const int b1 = t >> B2, b2 = t & (P2 - 1);
   const uint32_t f = tfirst[b1], k = tK[b1];
   uint64_t run = 0;
-  for (uint32_t j = 0; j < k; ++j) {
-    uint32_t x = hist2[(uint64_t)(f + j) * P2 + b2];
-    hist2[(uint64_t)(f + j) * P2 + b2] = (uint32_t)run;
-    run += x;
+  constexpr int R = 16;   // rows loaded together, so their latencies overlap
+  for (uint32_t j0 = 0; j0 < k; j0 += R) {
+    uint32_t x[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) x[j] = j0 + j < k ? hist2[(uint64_t)(f + j0 + j) * P2 + b2] : 0u;
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      if (j0 + j < k) hist2[(uint64_t)(f + j0 + j) * P2 + b2] = (uint32_t)run;
+      run += x[j];
+    }
   }
   tot2[t] = run;
 }
@@ -352,19 +385,27 @@ k_scatter2(const typename RecT<F>::type* in, const Tile* tiles, const unsigned i
   __syncwarp();
   const int sh = sub_shift<F>(B1, B2);
   const uint32_t lt = lanemask_lt();
-  for (uint64_t base = tl.begin; base < tl.end; base += 32) {
-    const uint64_t i = base + lane;
-    const bool v = i < tl.end;
-    uint32_t b = 0xFFFFFFFFu;
-    typename RecT<F>::type rec = 0;
-    if (v) { rec = in[i]; b = (uint32_t)((uint64_t)rec >> sh) & (P2 - 1); }
-    const uint32_t peers = match_bits<7>(b, v);
-    uint32_t pos = 0;
-    if (v) pos = cur[b] + __popc(peers & lt);
-    __syncwarp();
-    if (v && lane == __ffs(peers) - 1) cur[b] += __popc(peers);
-    __syncwarp();
-    if (v) out[pos] = rec;
+  for (uint64_t base = tl.begin; base < tl.end; base += 32 * BATCH) {
+    typename RecT<F>::type rec[BATCH];
+    uint32_t b[BATCH];
+#pragma unroll
+    for (int j = 0; j < BATCH; ++j) {
+      const uint64_t i = base + j * 32 + lane;
+      rec[j] = 0;
+      b[j] = 0xFFFFFFFFu;
+      if (i < tl.end) { rec[j] = in[i]; b[j] = (uint32_t)((uint64_t)rec[j] >> sh) & (P2 - 1); }
+    }
+#pragma unroll
+    for (int j = 0; j < BATCH; ++j) {
+      const bool v = b[j] != 0xFFFFFFFFu;
+      const uint32_t peers = match_bits<7>(b[j], v);
+      uint32_t pos = 0;
+      if (v) pos = cur[b[j]] + __popc(peers & lt);
+      __syncwarp();
+      if (v && lane == __ffs(peers) - 1) cur[b[j]] += __popc(peers);
+      __syncwarp();
+      if (v) out[pos] = rec[j];
+    }
   }
 }
 
@@ -681,52 +722,28 @@ k_fold(const typename RecT<F>::type* recs, const Tile* units, const unsigned int
   flush_final(p, fc);
 }
 
-// Single CTA: groups of up to GC consecutive items of every bucket still
-// holding K >= 2 items; a group whose bucket ends up with one group is final.
-__global__ void __launch_bounds__(1024)
-k_make_groups(const uint32_t* first_in, const uint32_t* K_in, int P, Group* groups, uint32_t* first_out,
-              uint32_t* K_out, unsigned int* n_groups) {
-  __shared__ uint32_t wsum[32];
-  const int t = threadIdx.x;
-  const int per = (P + 1023) / 1024;
-  const int b0 = min(P, t * per), b1 = min(P, b0 + per);
-  uint32_t s = 0;
-  for (int b = b0; b < b1; ++b) if (K_in[b] >= 2) s += (K_in[b] + GC - 1) / GC;
-  uint32_t x = s;
-  const int lane = t & 31, w = t >> 5;
-  for (int o = 1; o < 32; o <<= 1) {
-    uint32_t y = __shfl_up_sync(FULL, x, o);
-    if (lane >= o) x += y;
+// Groups of up to GC consecutive items of every bucket still holding K >= 2
+// items; a bucket that ends up with one group is finalised by it.
+__global__ void k_count_groups(const uint32_t* K_in, int P, uint32_t* K_out) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= P) return;
+  const uint32_t k = K_in[b];
+  K_out[b] = k >= 2 ? (k + GC - 1) / GC : 0u;
+}
+
+__global__ void k_emit_groups(const uint32_t* first_in, const uint32_t* K_in, int P, const uint32_t* first_out,
+                              const uint32_t* K_out, Group* groups) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= P) return;
+  const uint32_t k = K_in[b], g = K_out[b];
+  for (uint32_t j = 0; j < g; ++j) {
+    Group G;
+    G.bucket = (uint32_t)b;
+    G.first = first_in[b] + j * GC;
+    G.cnt = min((uint32_t)GC, k - j * GC);
+    G.k = j; G.K = g; G.pad = 0;
+    groups[first_out[b] + j] = G;
   }
-  if (lane == 31) wsum[w] = x;
-  __syncthreads();
-  if (w == 0) {
-    uint32_t z = wsum[lane];
-    for (int o = 1; o < 32; o <<= 1) {
-      uint32_t y = __shfl_up_sync(FULL, z, o);
-      if (lane >= o) z += y;
-    }
-    wsum[lane] = z;
-  }
-  __syncthreads();
-  uint32_t run = x - s + (w ? wsum[w - 1] : 0);
-  for (int b = b0; b < b1; ++b) {
-    const uint32_t k = K_in[b];
-    if (k < 2) { first_out[b] = 0; K_out[b] = k == 1 ? 0 : 0; continue; }
-    const uint32_t g = (k + GC - 1) / GC;
-    first_out[b] = run;
-    K_out[b] = g;
-    for (uint32_t j = 0; j < g; ++j) {
-      Group G;
-      G.bucket = (uint32_t)b;
-      G.first = first_in[b] + j * GC;
-      G.cnt = min((uint32_t)GC, k - j * GC);
-      G.k = j; G.K = g; G.pad = 0;
-      groups[run + j] = G;
-    }
-    run += g;
-  }
-  if (t == 1023) *n_groups = run;
 }
 
 struct CombineShared {
@@ -995,7 +1012,9 @@ static rv_status launch_all(const Plan& pl, const rv_formula* f, const void* key
       uint64_t* tot2 = (uint64_t*)(ws + pl.o_tot2);
       uint64_t* bstart2 = (uint64_t*)(ws + pl.o_bstart2);
       Rec* recB = (Rec*)(ws + pl.o_recB);
-      RV_LAUNCH("k_make_tiles", k_make_tiles, 1, 1024, 0, s, bstart1, pl.P1, TILE2, tiles2, tf2, tk2, &acc->n_tiles2);
+      RV_LAUNCH("k_count_tiles", k_count_tiles, (pl.P1 + 255) / 256, 256, 0, s, bstart1, pl.P1, (uint64_t)TILE2, tk2);
+      RV_LAUNCH("k_scan_u32", k_scan_u32, 1, 1024, 0, s, tk2, pl.P1, tf2, &acc->n_tiles2);
+      RV_LAUNCH("k_emit_tiles", k_emit_tiles, (int)((pl.max_tiles2 + 255) / 256), 256, 0, s, bstart1, pl.P1, (uint64_t)TILE2, tf2, tk2, &acc->n_tiles2, tiles2);
       const int t2_blocks = (int)((pl.max_tiles2 + SC_WARPS - 1) / SC_WARPS);
       RV_LAUNCH("k_hist2", k_hist2<F>, t2_blocks, SC_WARPS * 32, 0, s, recA, tiles2, &acc->n_tiles2, pl.B1, pl.B2, hist2);
       RV_LAUNCH("k_scan2", k_scan2, (pl.P + 255) / 256, 256, 0, s, hist2, tf2, tk2, pl.P1, pl.B2, tot2);
@@ -1012,7 +1031,9 @@ static rv_status launch_all(const Plan& pl, const rv_formula* f, const void* key
     Group* groups = (Group*)(ws + pl.o_groups);
     Pair* pool0 = (Pair*)(ws + pl.o_pool0);
     Pair* pool1 = (Pair*)(ws + pl.o_pool1);
-    RV_LAUNCH("k_make_tiles", k_make_tiles, 1, 1024, 0, s, bstart, pl.P, pl.unit, units, uf, uk, &acc->n_units);
+    RV_LAUNCH("k_count_tiles", k_count_tiles, (pl.P + 255) / 256, 256, 0, s, bstart, pl.P, pl.unit, uk);
+    RV_LAUNCH("k_scan_u32", k_scan_u32, 1, 1024, 0, s, uk, pl.P, uf, &acc->n_units);
+    RV_LAUNCH("k_emit_tiles", k_emit_tiles, (int)((pl.max_units + 255) / 256), 256, 0, s, bstart, pl.P, pl.unit, uf, uk, &acc->n_units, units);
     const int grid = (int)std::min<uint64_t>(pl.max_units, (uint64_t)num_sms() * 2);
     RV_LAUNCH("k_fold", k_fold<F>, grid, FOLD_THREADS, sizeof(FoldShared), s, recs, units, &acc->n_units, p, items0, pool0);
     const uint32_t* fin = uf;
@@ -1026,7 +1047,9 @@ static rv_status launch_all(const Plan& pl, const rv_formula* f, const void* key
     for (int l = 0; l < pl.levels; ++l) {
       const int dst = (l + 1) & 1;
       RV_CU(cudaMemsetAsync(&acc->pair_top[dst], 0, sizeof(unsigned long long), s));
-      RV_LAUNCH("k_make_groups", k_make_groups, 1, 1024, 0, s, fin, kin, pl.P, groups, gf[l & 1], gk[l & 1], &acc->n_groups[l]);
+      RV_LAUNCH("k_count_groups", k_count_groups, (pl.P + 255) / 256, 256, 0, s, kin, pl.P, gk[l & 1]);
+      RV_LAUNCH("k_scan_u32", k_scan_u32, 1, 1024, 0, s, gk[l & 1], pl.P, gf[l & 1], &acc->n_groups[l]);
+      RV_LAUNCH("k_emit_groups", k_emit_groups, (pl.P + 255) / 256, 256, 0, s, fin, kin, pl.P, gf[l & 1], gk[l & 1], groups);
       const int cgrid = (int)std::min<uint64_t>(pl.max_units / GC + pl.P, (uint64_t)num_sms() * 2);
       RV_LAUNCH("k_combine", k_combine<F>, cgrid, FOLD_THREADS, sizeof(CombineShared), s, iin, pin, groups, &acc->n_groups[l], &acc->next_group[l], p,
                                                                       iout, pout, dst);
