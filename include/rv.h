@@ -174,6 +174,38 @@ rv_status rv_verify_trace_async(const rv_formula* f, const rv_trace* t, void* ws
                                 rv_result* dev_out, const rv_bindings* bindings,
                                 const rv_verify_opts* opts, cudaStream_t s);
 
+/* ------------------------------------------------------------------ batched verification
+ * Many traces of uneven length, each checked against its own list of nf
+ * single-quantifier formulas (nf <= 32), in one fixed sequence of launches
+ * captured in a CUDA graph (Algorithm 1, with the grouping of a trace shared
+ * by all of its formulas).  The traces are concatenated: key uint32[n] and
+ * pred uint8[n] hold trace t at [offsets[t], offsets[t+1]).  Formula j of
+ * trace t is f[t * nf + j]; all formulas of a trace must have one quantifier,
+ * 32-bit keys and the trace's alphabet (at most 16 letters).
+ *   rv_batch_create: validate, copy the monitor tables, plan buckets and warp
+ *     tiles from the offsets (host arrays; copied).  Device memory for the
+ *     plan comes from the registered allocator (or cudaMalloc).
+ *   rv_batch_run: key/pred/ws/dev_results are device pointers; results
+ *     rv_result[nt * nf] land in dev_results after s completes.  The launch
+ *     sequence is captured once per argument set and replayed as a graph.
+ *     A result's status RV_EAGAIN means a bucket held more than 512 bindings:
+ *     rerun with a smaller bucket_records.
+ *   rv_batch_autotune: times the candidate bucket sizes and warp-tile lengths
+ *     on the given inputs, keeps the fastest and reports it in *chosen. */
+typedef struct rv_batch rv_batch;
+typedef struct {
+  int bucket_records;   /* target records per bucket (per trace), default 4096 */
+  int tile_events;      /* events per warp tile of the split, default 16384 */
+} rv_batch_opts;
+rv_status rv_batch_create(const rv_formula* const* f, int nf, int nt, const uint64_t* offsets,
+                          const rv_batch_opts* opts, rv_batch** out);
+size_t rv_batch_workspace_size(const rv_batch* b);
+rv_status rv_batch_run(rv_batch* b, const uint32_t* key, const uint8_t* pred, void* ws, size_t ws_bytes,
+                       rv_result* dev_results, cudaStream_t s);
+rv_status rv_batch_autotune(rv_batch* b, const uint32_t* key, const uint8_t* pred, void* ws, size_t ws_bytes,
+                            rv_result* dev_results, cudaStream_t s, rv_batch_opts* chosen);
+void rv_batch_free(rv_batch* b);
+
 /* ------------------------------------------------------------------ instrumentation
  * The paper times whole monitor runs (Sec. 5.2); these calls time each kernel.
  * rv_profile_enable(1): every kernel launch of the library is bracketed by a

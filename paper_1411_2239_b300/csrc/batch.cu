@@ -1,0 +1,747 @@
+// Batched verification: many traces of uneven length, each checked against
+// its own list of up to 32 single-quantifier formulas, in one fixed sequence
+// of launches that is captured once in a CUDA graph and replayed.
+//
+// Layout: the traces are concatenated (key uint32[n], pred uint8[n]) with CSR
+// offsets; trace t owns events offsets[t]..offsets[t+1].  The formulas of a
+// trace all quantify the same key, so the trace is grouped once and every
+// binding's events are read once for all its formulas (Algorithm 1 with the
+// SortTrace/SpawnMonitors work shared by the formulas of a trace).
+//
+// map      k_bhist / k_bscan / k_bucket_scan / k_bscatter: each trace gets
+//          2^bits_t buckets by the top bits of mix32(key) (bits_t from its
+//          length and the autotuned target bucket size), so buckets never mix
+//          traces.  Warp tiles never cross a trace boundary and keep private
+//          cursors, so records keep trace order inside each bucket.
+// monitor  k_bfold: per bucket, chunks of records are stably counting-sorted
+//          by binding slot in shared memory; then warps walk the bindings'
+//          letter runs with lane f stepping formula f's monitor (states in
+//          shared memory between chunks, in registers along a run).
+// reduce   per (trace, formula) verdict counts; k_broot applies each
+//          formula's quantifier constraint (exact integers).
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "profile.h"
+#include "rv_device.cuh"
+
+using namespace rvd;
+
+void* rv_dev_alloc(size_t bytes);
+void rv_dev_free(void* p);
+
+namespace {
+
+constexpr unsigned FULL = 0xFFFFFFFFu;
+constexpr int BW = 4;                 // warps per CTA in the split kernels (32 KB of cursors)
+constexpr int BATCHR = 16;            // load batching
+constexpr int MAXF = 32;              // formulas per trace (one per lane)
+constexpr int MAXL = 16;              // letters per formula in batched mode
+constexpr int MAXBITS = 11;           // at most 2048 buckets per trace
+constexpr int FW = 4;                 // warps per CTA in k_bfold
+constexpr int CHUNK = 4096;           // records sorted at once in k_bfold
+constexpr int BSLOTS = 512;           // bindings per bucket held in shared memory
+constexpr int BHT_BITS = 10;
+constexpr int BHT = 1 << BHT_BITS;
+constexpr uint16_t NO_SLOT = 0xFFFF, FULL_SLOT = 0xFFFE;
+constexpr uint32_t EMPTY32 = 0xFFFFFFFFu;
+
+struct WTile { uint32_t trace, nb; uint64_t begin, end, hist_off; };
+
+struct BatchDev {
+  const WTile* tiles;
+  const uint32_t* bucket_base;   // [nt+1] first global bucket of trace t
+  const uint32_t* bucket_trace;  // [NB] trace of global bucket
+  const uint32_t* trace_bits;    // [nt]
+  const uint32_t* tile_first;    // [nt+1] first warp tile of trace t
+  const uint64_t* maps;          // [nt][MAXL][MAXF]
+  const uint8_t* labels;         // [nt][MAXF][16]
+  const rv_quant* quants;        // [nt][MAXF]
+  const uint32_t* nletters;      // [nt]
+  const uint64_t* offsets;       // [nt+1]
+  int nt, nf, NB, ntiles;
+};
+
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+template <int BITS>
+__device__ __forceinline__ uint32_t match_bits(uint32_t v, bool valid) {
+  const uint32_t vb = __ballot_sync(FULL, valid);
+  uint32_t m = valid ? vb : ~vb;
+#pragma unroll
+  for (int k = 0; k < BITS; ++k) {
+    const uint32_t bk = __ballot_sync(FULL, (v >> k) & 1u);
+    m &= ((v >> k) & 1u) ? bk : ~bk;
+  }
+  return m;
+}
+
+__device__ __forceinline__ uint32_t bucket_of(uint32_t key, uint32_t bits) {
+  return bits ? mix32(key) >> (32 - bits) : 0u;
+}
+
+__global__ void __launch_bounds__(BW * 32)
+k_bhist(BatchDev d, const uint32_t* key, const uint8_t* pred, uint32_t* hist, unsigned int* err) {
+  __shared__ uint32_t cnt_all[BW][1 << MAXBITS];
+  const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tile = blockIdx.x * BW + wl;
+  if (tile >= d.ntiles) return;
+  const WTile T = d.tiles[tile];
+  const uint32_t bits = d.trace_bits[T.trace], nl = d.nletters[T.trace];
+  uint32_t* cnt = cnt_all[wl];
+  for (uint32_t b = lane; b < T.nb; b += 32) cnt[b] = 0;
+  __syncwarp();
+  bool bad = false;
+  for (uint64_t base = T.begin; base < T.end; base += 32 * BATCHR) {
+    uint32_t b[BATCHR];
+#pragma unroll
+    for (int j = 0; j < BATCHR; ++j) {
+      const uint64_t i = base + j * 32 + lane;
+      b[j] = EMPTY32;
+      if (i < T.end) {
+        b[j] = bucket_of(key[i], bits);
+        if (pred[i] >= nl) bad = true;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < BATCHR; ++j)
+      if (b[j] != EMPTY32) atomicAdd(&cnt[b[j]], 1u);
+  }
+  if (__any_sync(FULL, bad) && lane == 0) atomicOr(err, (unsigned)ERR_LETTER);
+  __syncwarp();
+  for (uint32_t b = lane; b < T.nb; b += 32) hist[T.hist_off + b] = cnt[b];
+}
+
+// one thread per global bucket: exclusive prefix over the tiles of its trace
+__global__ void k_bscan(BatchDev d, uint32_t* hist, uint64_t* tot) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= d.NB) return;
+  const uint32_t t = d.bucket_trace[g];
+  const uint32_t b = g - d.bucket_base[t];
+  const uint32_t t0 = d.tile_first[t], t1 = d.tile_first[t + 1];
+  uint64_t run = 0;
+  constexpr int R = 16;
+  for (uint32_t j0 = t0; j0 < t1; j0 += R) {
+    uint32_t x[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) x[j] = j0 + j < t1 ? hist[d.tiles[j0 + j].hist_off + b] : 0u;
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      if (j0 + j < t1) hist[d.tiles[j0 + j].hist_off + b] = (uint32_t)run;
+      run += x[j];
+    }
+  }
+  tot[g] = run;
+}
+
+__global__ void __launch_bounds__(1024) k_scan64(const uint64_t* tot, int P, uint64_t* out) {
+  __shared__ uint64_t wsum[32];
+  __shared__ uint64_t carry;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  if (t == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < P; base += 4096) {
+    uint64_t v[4], s = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int i = base + t * 4 + j;
+      v[j] = i < P ? tot[i] : 0ull;
+      s += v[j];
+    }
+    uint64_t x = s;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint64_t y = __shfl_up_sync(FULL, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    if (w == 0) {
+      uint64_t z = wsum[lane];
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t y = __shfl_up_sync(FULL, z, o);
+        if (lane >= o) z += y;
+      }
+      wsum[lane] = z;
+    }
+    __syncthreads();
+    uint64_t run = carry + x - s + (w ? wsum[w - 1] : 0ull);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int i = base + t * 4 + j;
+      if (i < P) out[i] = run;
+      run += v[j];
+    }
+    __syncthreads();
+    if (t == 1023) carry = run;
+    __syncthreads();
+  }
+  if (t == 0) out[P] = carry;
+}
+
+__global__ void __launch_bounds__(BW * 32)
+k_bscatter(BatchDev d, const uint32_t* key, const uint8_t* pred, const uint32_t* pre, const uint64_t* bstart,
+           uint64_t* recs) {
+  __shared__ uint32_t cur_all[BW][1 << MAXBITS];
+  const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tile = blockIdx.x * BW + wl;
+  if (tile >= d.ntiles) return;
+  const WTile T = d.tiles[tile];
+  const uint32_t bits = d.trace_bits[T.trace], nl = d.nletters[T.trace];
+  const uint32_t gb = d.bucket_base[T.trace];
+  uint32_t* cur = cur_all[wl];
+  for (uint32_t b = lane; b < T.nb; b += 32) cur[b] = (uint32_t)(bstart[gb + b] + pre[T.hist_off + b]);
+  __syncwarp();
+  const uint32_t lt = lanemask_lt();
+  for (uint64_t base = T.begin; base < T.end; base += 32 * BATCHR) {
+    uint32_t b[BATCHR];
+    uint64_t r[BATCHR];
+#pragma unroll
+    for (int j = 0; j < BATCHR; ++j) {
+      const uint64_t i = base + j * 32 + lane;
+      b[j] = EMPTY32;
+      r[j] = 0;
+      if (i < T.end) {
+        const uint32_t k = key[i];
+        uint32_t l = pred[i];
+        if (l >= nl) l = 0;
+        b[j] = bucket_of(k, bits);
+        r[j] = ((uint64_t)k << 8) | l;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < BATCHR; ++j) {
+      const bool v = b[j] != EMPTY32;
+      const uint32_t peers = match_bits<MAXBITS>(b[j], v);
+      uint32_t pos = 0;
+      if (v) pos = cur[b[j]] + __popc(peers & lt);
+      __syncwarp();
+      if (v && lane == __ffs(peers) - 1) cur[b[j]] += __popc(peers);
+      __syncwarp();
+      if (v) recs[pos] = r[j];
+    }
+  }
+}
+
+// ------------------------------------------------------------------ fold of one bucket
+struct BFoldShared {
+  uint64_t lmap[MAXL][MAXF];
+  uint8_t labels[MAXF][16];
+  uint64_t tkey[BHT];            // key | 1 << 32 once claimed, 0 when empty
+  uint16_t tslot[BHT];
+  uint8_t state[BSLOTS][MAXF];
+  uint16_t slot_of[CHUNK];
+  uint8_t letter[CHUNK];
+  uint8_t sorted[CHUNK];
+  uint32_t wcnt[FW][BSLOTS];     // per-warp counts, then per-warp cursors
+  uint32_t seg[BSLOTS + 1];
+  uint32_t fcount[MAXF][6];
+  uint32_t tsum[FW * 32];
+  unsigned int nslots, ovf, next;
+};
+
+__device__ int bfind_or_insert(BFoldShared& S, uint32_t key, unsigned int* err) {
+  const uint64_t tag = (uint64_t)key | (1ull << 32);
+  uint32_t h = (key * 0x9E3779B9u) >> (32 - BHT_BITS);
+  volatile uint64_t* vk = S.tkey;
+  volatile uint16_t* vs = S.tslot;
+  for (int probe = 0; probe < BHT; ++probe) {
+    uint64_t k = vk[h];
+    if (k == 0) {
+      const unsigned long long prev = atomicCAS((unsigned long long*)&S.tkey[h], 0ull, (unsigned long long)tag);
+      if (prev == 0) {
+        const unsigned int s = atomicAdd(&S.nslots, 1u);
+        if (s >= BSLOTS) { S.ovf = 1; __threadfence_block(); vs[h] = FULL_SLOT; return -1; }
+        for (int f = 0; f < MAXF; ++f) S.state[s][f] = 0;   // q0 = 0 for every compiled monitor
+        __threadfence_block();
+        vs[h] = (uint16_t)s;
+        return (int)s;
+      }
+      k = prev;
+    }
+    if (k == tag) {
+      uint16_t s;
+      int spins = 0;
+      while ((s = vs[h]) == NO_SLOT) {
+        if (++spins > (1 << 22)) { atomicOr(err, (unsigned)ERR_SPIN); return -1; }
+      }
+      return s == FULL_SLOT ? -1 : (int)s;
+    }
+    h = (h + 1) & (BHT - 1);
+  }
+  S.ovf = 1;
+  return -1;
+}
+
+constexpr unsigned ERR_BUCKET = 32;   // a bucket has more than BSLOTS bindings
+
+__global__ void __launch_bounds__(FW * 32)
+k_bfold(BatchDev d, const uint64_t* recs, const uint64_t* bstart, unsigned long long* counts,
+        unsigned long long* nbind, unsigned int* err, unsigned int* next) {
+  extern __shared__ __align__(16) unsigned char bsm[];
+  BFoldShared& S = *reinterpret_cast<BFoldShared*>(bsm);
+  const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31, nthr = FW * 32;
+  const uint32_t lt = lanemask_lt();
+  const int nf = d.nf;
+  while (true) {
+    __syncthreads();
+    if (threadIdx.x == 0) S.next = atomicAdd(next, 1u);
+    __syncthreads();
+    const unsigned int g = S.next;
+    if (g >= (unsigned)d.NB) break;
+    const uint64_t b0 = bstart[g], b1 = bstart[g + 1];
+    if (b0 == b1) continue;
+    const uint32_t t = d.bucket_trace[g];
+    for (int i = threadIdx.x; i < MAXL * MAXF; i += nthr)
+      S.lmap[i / MAXF][i % MAXF] = d.maps[(uint64_t)t * MAXL * MAXF + i];
+    for (int i = threadIdx.x; i < MAXF * 16; i += nthr) S.labels[i / 16][i % 16] = d.labels[(uint64_t)t * MAXF * 16 + i];
+    for (int i = threadIdx.x; i < BHT; i += nthr) { S.tkey[i] = 0; S.tslot[i] = NO_SLOT; }
+    for (int i = threadIdx.x; i < MAXF * 6; i += nthr) S.fcount[i / 6][i % 6] = 0;
+    if (threadIdx.x == 0) { S.nslots = 0; S.ovf = 0; }
+    __syncthreads();
+    bool failed = false;
+    for (uint64_t c0 = b0; c0 < b1; c0 += CHUNK) {
+      const int cn = (int)min((uint64_t)CHUNK, b1 - c0);
+      // 1. binding slot of every record of the chunk
+      for (int i = threadIdx.x; i < cn; i += nthr) {
+        const uint64_t r = recs[c0 + i];
+        const int sl = bfind_or_insert(S, (uint32_t)(r >> 8), err);
+        S.slot_of[i] = (uint16_t)(sl < 0 ? 0 : sl);
+        S.letter[i] = (uint8_t)(r & 0xFF);
+      }
+      for (int i = threadIdx.x; i < FW * BSLOTS; i += nthr) S.wcnt[i / BSLOTS][i % BSLOTS] = 0;
+      __syncthreads();
+      if (S.ovf) { failed = true; break; }
+      const int nsl = (int)S.nslots;
+      // 2. stable counting sort by slot; warp w owns records [w0, w1) of the chunk
+      const int per = (cn + FW - 1) / FW;
+      const int w0 = min(cn, wl * per), w1 = min(cn, w0 + per);
+      for (int i = w0 + lane; i < w1; i += 32) atomicAdd(&S.wcnt[wl][S.slot_of[i]], 1u);
+      __syncthreads();
+      // exclusive scan over (slot, warp): each thread owns 4 consecutive slots
+      {
+        const int s0 = threadIdx.x * 4;
+        uint32_t tot[4], sum = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int sl = s0 + j;
+          uint32_t x = 0;
+          if (sl < BSLOTS)
+            for (int w = 0; w < FW; ++w) x += S.wcnt[w][sl];
+          tot[j] = x;
+          sum += x;
+        }
+        uint32_t x = sum;
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(FULL, x, o);
+          if (lane >= o) x += y;
+        }
+        if (lane == 31) S.tsum[wl] = x;
+        __syncthreads();
+        uint32_t wbase = 0;
+        for (int w = 0; w < wl; ++w) wbase += S.tsum[w];
+        uint32_t run = wbase + x - sum;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int sl = s0 + j;
+          if (sl < BSLOTS) {
+            S.seg[sl] = run;
+            uint32_t r2 = run;
+            for (int w = 0; w < FW; ++w) { const uint32_t c = S.wcnt[w][sl]; S.wcnt[w][sl] = r2; r2 += c; }
+          }
+          run += tot[j];
+        }
+        if (threadIdx.x == 0) S.seg[BSLOTS] = (uint32_t)cn;
+      }
+      __syncthreads();
+      for (int base = w0; base < w1; base += 32) {
+        const int i = base + lane;
+        const bool v = i < w1;
+        const uint32_t sl = v ? S.slot_of[i] : 0u;
+        const uint32_t peers = match_bits<10>(sl, v);
+        uint32_t pos = 0;
+        if (v) pos = S.wcnt[wl][sl] + __popc(peers & lt);
+        __syncwarp();
+        if (v && lane == __ffs(peers) - 1) S.wcnt[wl][sl] += __popc(peers);
+        __syncwarp();
+        if (v) S.sorted[pos] = S.letter[i];
+      }
+      __syncthreads();
+      // 3. walk every binding's letters: lane f steps formula f
+      for (int sl = wl; sl < nsl; sl += FW) {
+        const uint32_t lo = S.seg[sl], hi = (sl + 1 < BSLOTS) ? S.seg[sl + 1] : (uint32_t)cn;
+        uint32_t st = S.state[sl][lane];
+        for (uint32_t base = lo; base < hi; base += 32) {
+          const uint32_t n = min(32u, hi - base);
+          const uint32_t mine = lane < n ? S.sorted[base + lane] : 0u;
+          for (uint32_t j = 0; j < n; ++j) {
+            const uint32_t l = __shfl_sync(FULL, mine, j);
+            st = (uint32_t)((S.lmap[l][lane] >> (4 * st)) & 15ull);
+          }
+        }
+        S.state[sl][lane] = (uint8_t)st;
+      }
+      __syncthreads();
+    }
+    if (failed) {
+      if (threadIdx.x == 0) atomicOr(err, ERR_BUCKET);
+      continue;
+    }
+    // 4. verdict counts per formula
+    uint32_t c[6] = {0, 0, 0, 0, 0, 0};
+    const int nsl = (int)S.nslots;
+    for (int sl = wl; sl < nsl; sl += FW) {
+      const uint32_t v = S.labels[lane][S.state[sl][lane] & 15];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) c[k] += v == (uint32_t)k;
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+      if (c[k]) atomicAdd(&S.fcount[lane][k], c[k]);
+    __syncthreads();
+    for (int i = threadIdx.x; i < nf * 6; i += nthr) {
+      const uint32_t x = S.fcount[i / 6][i % 6];
+      if (x) atomicAdd(&counts[((uint64_t)t * nf + i / 6) * 6 + i % 6], (unsigned long long)x);
+    }
+    if (threadIdx.x == 0) atomicAdd(&nbind[t], (unsigned long long)nsl);
+  }
+}
+
+__global__ void k_broot(BatchDev d, const unsigned long long* counts, const unsigned long long* nbind,
+                        const unsigned int* err, rv_result* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.nt * d.nf) return;
+  const int t = i / d.nf;
+  rv_result r;
+  memset(&r, 0, sizeof r);
+  uint64_t v[6];
+  for (int k = 0; k < 6; ++k) v[k] = counts[(uint64_t)i * 6 + k];
+  const rv_quant q = d.quants[(uint64_t)t * MAXF + i % d.nf];
+  r.root = rvv::valuate(q.kind, q.op, q.num, q.den, v);
+  for (int k = 0; k < 6; ++k) { r.root_counts[k] = v[k]; r.level_counts[0][k] = v[k]; }
+  r.n_nodes[0] = nbind[t];
+  r.events = d.offsets[t + 1] - d.offsets[t];
+  const unsigned e = *err;
+  r.status = (e & ERR_LETTER) ? RV_EINVAL : (e & ERR_BUCKET) ? RV_EAGAIN : e ? RV_EINTERNAL : RV_OK;
+  out[i] = r;
+}
+
+#define BCU(call)                                                                              \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess) return rv_fail(RV_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+}  // namespace
+
+// ------------------------------------------------------------------ host side
+struct rv_batch {
+  int nt = 0, nf = 0;
+  std::vector<uint64_t> offsets;
+  std::vector<uint64_t> maps;     // [nt][MAXL][MAXF]
+  std::vector<uint8_t> labels;    // [nt][MAXF][16]
+  std::vector<rv_quant> quants;   // [nt][MAXF]
+  std::vector<uint32_t> nletters; // [nt]
+  int bucket_records = 4096;
+  int tile_events = 16384;
+  // device plan (rebuilt when the tuning changes)
+  void* plan = nullptr;
+  size_t plan_bytes = 0;
+  BatchDev dev{};
+  size_t hist_entries = 0;
+  // captured graph and the arguments it was captured with
+  cudaGraphExec_t exec = nullptr;
+  const void* g_key = nullptr;
+  const void* g_pred = nullptr;
+  const void* g_ws = nullptr;
+  const void* g_res = nullptr;
+  cudaStream_t cap = nullptr;
+};
+
+namespace {
+
+struct BatchLayout {
+  size_t o_hist, o_tot, o_bstart, o_recs, o_counts, o_nbind, o_err, o_next, total;
+};
+
+size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+void plan_shape(const rv_batch* b, int bucket_records, int tile_events, std::vector<uint32_t>* bits,
+                std::vector<WTile>* tiles, int* NB, size_t* hist_entries) {
+  int nb_total = 0;
+  size_t hist = 0;
+  for (int t = 0; t < b->nt; ++t) {
+    const uint64_t len = b->offsets[t + 1] - b->offsets[t];
+    uint32_t k = 0;
+    while (k < (uint32_t)MAXBITS && (len >> k) > (uint64_t)bucket_records) ++k;
+    if (bits) bits->push_back(k);
+    const uint32_t nb = 1u << k;
+    for (uint64_t s = b->offsets[t]; s < b->offsets[t + 1]; s += (uint64_t)tile_events) {
+      if (tiles) tiles->push_back(WTile{(uint32_t)t, nb, s, std::min(b->offsets[t + 1], s + (uint64_t)tile_events), hist});
+      hist += nb;
+    }
+    nb_total += (int)nb;
+  }
+  *NB = nb_total;
+  *hist_entries = hist;
+}
+
+BatchLayout layout(const rv_batch* b, int NB, size_t hist_entries) {
+  BatchLayout L{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t r = off; off = a256(off + bytes); return r; };
+  const uint64_t n = b->offsets.back();
+  L.o_hist = take(std::max<size_t>(hist_entries, 1) * 4);
+  L.o_tot = take((size_t)NB * 8);
+  L.o_bstart = take((size_t)(NB + 1) * 8);
+  L.o_recs = take(std::max<uint64_t>(n, 1) * 8);
+  L.o_counts = take((size_t)b->nt * b->nf * 6 * 8);
+  L.o_nbind = take((size_t)b->nt * 8);
+  L.o_err = take(4);
+  L.o_next = take(4);
+  L.total = off;
+  return L;
+}
+
+rv_status build_plan(rv_batch* b) {
+  std::vector<uint32_t> bits;
+  std::vector<WTile> tiles;
+  int NB = 0;
+  size_t hist_entries = 0;
+  plan_shape(b, b->bucket_records, b->tile_events, &bits, &tiles, &NB, &hist_entries);
+  std::vector<uint32_t> base(b->nt + 1), btrace(NB), tfirst(b->nt + 1);
+  int g = 0;
+  for (int t = 0; t < b->nt; ++t) {
+    base[t] = (uint32_t)g;
+    for (uint32_t j = 0; j < (1u << bits[t]); ++j) btrace[g++] = (uint32_t)t;
+  }
+  base[b->nt] = (uint32_t)g;
+  size_t ti = 0;
+  for (int t = 0; t < b->nt; ++t) {
+    tfirst[t] = (uint32_t)ti;
+    while (ti < tiles.size() && tiles[ti].trace == (uint32_t)t) ++ti;
+  }
+  tfirst[b->nt] = (uint32_t)ti;
+  // one device block for every plan array
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t r = off; off = a256(off + bytes); return r; };
+  const size_t o_tiles = take(std::max<size_t>(tiles.size(), 1) * sizeof(WTile));
+  const size_t o_base = take(base.size() * 4), o_btrace = take(btrace.size() * 4), o_bits = take(bits.size() * 4 + 4);
+  const size_t o_tfirst = take(tfirst.size() * 4), o_maps = take(b->maps.size() * 8),
+               o_labels = take(b->labels.size()), o_quants = take(b->quants.size() * sizeof(rv_quant)),
+               o_nl = take(b->nletters.size() * 4), o_offs = take(b->offsets.size() * 8);
+  if (b->plan) { rv_dev_free(b->plan); b->plan = nullptr; }
+  b->plan = rv_dev_alloc(off);
+  if (!b->plan) return rv_fail(RV_ENOMEM, "cannot allocate %zu bytes for the batch plan", off);
+  b->plan_bytes = off;
+  unsigned char* P = (unsigned char*)b->plan;
+  BCU(cudaMemcpy(P + o_tiles, tiles.data(), tiles.size() * sizeof(WTile), cudaMemcpyHostToDevice));
+  BCU(cudaMemcpy(P + o_base, base.data(), base.size() * 4, cudaMemcpyHostToDevice));
+  BCU(cudaMemcpy(P + o_btrace, btrace.data(), btrace.size() * 4, cudaMemcpyHostToDevice));
+  BCU(cudaMemcpy(P + o_bits, bits.data(), bits.size() * 4, cudaMemcpyHostToDevice));
+  BCU(cudaMemcpy(P + o_tfirst, tfirst.data(), tfirst.size() * 4, cudaMemcpyHostToDevice));
+  BCU(cudaMemcpy(P + o_maps, b->maps.data(), b->maps.size() * 8, cudaMemcpyHostToDevice));
+  BCU(cudaMemcpy(P + o_labels, b->labels.data(), b->labels.size(), cudaMemcpyHostToDevice));
+  BCU(cudaMemcpy(P + o_quants, b->quants.data(), b->quants.size() * sizeof(rv_quant), cudaMemcpyHostToDevice));
+  BCU(cudaMemcpy(P + o_nl, b->nletters.data(), b->nletters.size() * 4, cudaMemcpyHostToDevice));
+  BCU(cudaMemcpy(P + o_offs, b->offsets.data(), b->offsets.size() * 8, cudaMemcpyHostToDevice));
+  BatchDev& d = b->dev;
+  d.tiles = (const WTile*)(P + o_tiles);
+  d.bucket_base = (const uint32_t*)(P + o_base);
+  d.bucket_trace = (const uint32_t*)(P + o_btrace);
+  d.trace_bits = (const uint32_t*)(P + o_bits);
+  d.tile_first = (const uint32_t*)(P + o_tfirst);
+  d.maps = (const uint64_t*)(P + o_maps);
+  d.labels = (const uint8_t*)(P + o_labels);
+  d.quants = (const rv_quant*)(P + o_quants);
+  d.nletters = (const uint32_t*)(P + o_nl);
+  d.offsets = (const uint64_t*)(P + o_offs);
+  d.nt = b->nt;
+  d.nf = b->nf;
+  d.NB = NB;
+  d.ntiles = (int)tiles.size();
+  b->hist_entries = hist_entries;
+  if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+  return RV_OK;
+}
+
+int num_sms_b() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      sms = 148;
+  }
+  return sms;
+}
+
+rv_status enqueue(rv_batch* b, const uint32_t* key, const uint8_t* pred, unsigned char* ws, rv_result* res,
+                  cudaStream_t s) {
+  const BatchDev& d = b->dev;
+  const BatchLayout L = layout(b, d.NB, b->hist_entries);
+  uint32_t* hist = (uint32_t*)(ws + L.o_hist);
+  uint64_t* tot = (uint64_t*)(ws + L.o_tot);
+  uint64_t* bstart = (uint64_t*)(ws + L.o_bstart);
+  uint64_t* recs = (uint64_t*)(ws + L.o_recs);
+  unsigned long long* counts = (unsigned long long*)(ws + L.o_counts);
+  unsigned long long* nbind = (unsigned long long*)(ws + L.o_nbind);
+  unsigned int* err = (unsigned int*)(ws + L.o_err);
+  unsigned int* next = (unsigned int*)(ws + L.o_next);
+  BCU(cudaMemsetAsync(ws + L.o_counts, 0, L.total - L.o_counts, s));   // counts, nbind, err, next
+  const int tb = (d.ntiles + BW - 1) / BW;
+  if (d.ntiles) {
+    RV_LAUNCH("k_bhist", k_bhist, tb, BW * 32, 0, s, d, key, pred, hist, err);
+    RV_LAUNCH("k_bscan", k_bscan, (d.NB + 255) / 256, 256, 0, s, d, hist, tot);
+    RV_LAUNCH("k_scan64", k_scan64, 1, 1024, 0, s, tot, d.NB, bstart);
+    RV_LAUNCH("k_bscatter", k_bscatter, tb, BW * 32, 0, s, d, key, pred, hist, bstart, recs);
+    const int grid = std::min(d.NB, num_sms_b() * 4);
+    RV_LAUNCH("k_bfold", k_bfold, grid, FW * 32, sizeof(BFoldShared), s, d, recs, bstart, counts, nbind, err, next);
+  }
+  RV_LAUNCH("k_broot", k_broot, (d.nt * d.nf + 127) / 128, 128, 0, s, d, counts, nbind, err, res);
+  BCU(cudaGetLastError());
+  return RV_OK;
+}
+
+}  // namespace
+
+extern "C" rv_status rv_batch_create(const rv_formula* const* f, int nf, int nt, const uint64_t* offsets,
+                                     const rv_batch_opts* opts, rv_batch** out) {
+  if (!f || !offsets || !out || nf < 1 || nf > MAXF || nt < 1)
+    return rv_fail(RV_EINVAL, "batch needs 1..32 formulas per trace and at least one trace");
+  *out = nullptr;
+  for (int t = 0; t < nt; ++t)
+    if (offsets[t + 1] < offsets[t]) return rv_fail(RV_EINVAL, "offsets must be non-decreasing");
+  if (offsets[0] != 0) return rv_fail(RV_EINVAL, "offsets[0] must be 0");
+  if (offsets[nt] > 0xFFFFFFFFull) return rv_fail(RV_EINVAL, "a batch is limited to 2^32-1 events");
+  rv_batch* b = new (std::nothrow) rv_batch();
+  if (!b) return rv_fail(RV_ENOMEM, "out of host memory");
+  b->nt = nt;
+  b->nf = nf;
+  b->offsets.assign(offsets, offsets + nt + 1);
+  b->maps.assign((size_t)nt * MAXL * MAXF, IDENTITY_MAP);
+  b->labels.assign((size_t)nt * MAXF * 16, 0);
+  b->quants.assign((size_t)nt * MAXF, rv_quant{RV_Q_E, RV_GE, 1, 1});
+  b->nletters.assign(nt, 0);
+  for (int t = 0; t < nt; ++t) {
+    for (int j = 0; j < nf; ++j) {
+      const rv_formula* F = f[(size_t)t * nf + j];
+      if (!F || F->n_quant != 1 || F->key_bits != 32 || F->n_letters > MAXL) {
+        delete b;
+        return rv_fail(RV_EUNSUPPORTED, "batched formulas need one quantifier, 32-bit keys and at most 16 letters");
+      }
+      if (j == 0) b->nletters[t] = (uint32_t)F->n_letters;
+      else if (b->nletters[t] != (uint32_t)F->n_letters) {
+        delete b;
+        return rv_fail(RV_EINVAL, "the formulas of one trace must share its alphabet");
+      }
+      for (int l = 0; l < F->n_letters; ++l) b->maps[((size_t)t * MAXL + l) * MAXF + j] = F->maps[l];
+      for (int s = 0; s < 16; ++s) b->labels[((size_t)t * MAXF + j) * 16 + s] = F->labels[s];
+      b->quants[(size_t)t * MAXF + j] = F->q[0];
+    }
+  }
+  if (opts && opts->bucket_records) b->bucket_records = opts->bucket_records;
+  if (opts && opts->tile_events) b->tile_events = std::max(1024, opts->tile_events);
+  rv_status st = build_plan(b);
+  if (st) { rv_batch_free(b); return st; }
+  *out = b;
+  return RV_OK;
+}
+
+extern "C" size_t rv_batch_workspace_size(const rv_batch* b) {
+  if (!b) return 0;
+  size_t worst = 0;
+  for (int br : {256, 512, 1024, 2048, 4096, 8192, b->bucket_records})
+    for (int te : {8192, 16384, 32768, b->tile_events}) {
+      int NB = 0;
+      size_t he = 0;
+      plan_shape(b, br, te, nullptr, nullptr, &NB, &he);
+      worst = std::max(worst, layout(b, NB, he).total);
+    }
+  return worst;
+}
+
+static bool g_bfold_attr = false;
+
+extern "C" rv_status rv_batch_run(rv_batch* b, const uint32_t* key, const uint8_t* pred, void* ws, size_t ws_bytes,
+                                  rv_result* dev_results, cudaStream_t s) {
+  if (!b || !ws || !dev_results || (b->offsets.back() && (!key || !pred)))
+    return rv_fail(RV_EINVAL, "null argument");
+  const BatchLayout L = layout(b, b->dev.NB, b->hist_entries);
+  if (ws_bytes < L.total) return rv_fail(RV_ENOMEM, "workspace of %zu bytes, need %zu", ws_bytes, L.total);
+  if (!g_bfold_attr) {
+    BCU(cudaFuncSetAttribute(k_bfold, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BFoldShared)));
+    g_bfold_attr = true;
+  }
+  if (!b->exec || b->g_key != key || b->g_pred != pred || b->g_ws != ws || b->g_res != dev_results) {
+    if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+    if (!b->cap) BCU(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
+    BCU(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+    rv_status st = enqueue(b, key, pred, (unsigned char*)ws, dev_results, b->cap);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(b->cap, &graph);
+    if (st) { if (graph) cudaGraphDestroy(graph); return st; }
+    if (e != cudaSuccess) return rv_fail(RV_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&b->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) { b->exec = nullptr; return rv_fail(RV_ECUDA, "graph instantiate: %s", cudaGetErrorString(e)); }
+    b->g_key = key; b->g_pred = pred; b->g_ws = ws; b->g_res = dev_results;
+  }
+  BCU(cudaGraphLaunch(b->exec, s));
+  rv_count_launch();
+  return RV_OK;
+}
+
+extern "C" rv_status rv_batch_autotune(rv_batch* b, const uint32_t* key, const uint8_t* pred, void* ws,
+                                       size_t ws_bytes, rv_result* dev_results, cudaStream_t s,
+                                       rv_batch_opts* chosen) {
+  if (!b || !dev_results) return rv_fail(RV_EINVAL, "null argument");
+  const int cand_br[] = {1024, 2048, 4096, 8192};
+  const int cand_te[] = {8192, 32768};
+  float best = 1e30f;
+  int best_br = b->bucket_records, best_te = b->tile_events;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  rv_status st = RV_OK;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    st = rv_fail(RV_ECUDA, "event creation failed");
+  for (int br : cand_br) {
+    for (int te : cand_te) {
+      if (st) break;
+      b->bucket_records = br;
+      b->tile_events = te;
+      if ((st = build_plan(b))) break;
+      if ((st = rv_batch_run(b, key, pred, ws, ws_bytes, dev_results, s))) break;   // capture + warm-up
+      float ms = 0.f;
+      if (cudaEventRecord(e0, s) != cudaSuccess) { st = rv_fail(RV_ECUDA, "event record"); break; }
+      for (int r = 0; r < 3 && !st; ++r) st = rv_batch_run(b, key, pred, ws, ws_bytes, dev_results, s);
+      if (st || cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+          cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        if (!st) st = rv_fail(RV_ECUDA, "timing failed");
+        break;
+      }
+      if (ms < best) { best = ms; best_br = br; best_te = te; }
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  b->bucket_records = best_br;
+  b->tile_events = best_te;
+  const rv_status st2 = build_plan(b);
+  if (chosen) { chosen->bucket_records = best_br; chosen->tile_events = best_te; }
+  return st ? st : st2;
+}
+
+extern "C" void rv_batch_free(rv_batch* b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  if (b->plan) rv_dev_free(b->plan);
+  delete b;
+}

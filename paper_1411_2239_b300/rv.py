@@ -276,3 +276,68 @@ def verify_async(formula: Formula, key, pred, ws, dev_result, stream=None, opts=
 def parse_result(raw: bytes) -> Result:
     r = _Result.from_buffer_copy(raw)
     return _result(r)
+
+
+# ---------------------------------------------------------------------- batched
+class _BatchOpts(ctypes.Structure):
+    _fields_ = [("bucket_records", ctypes.c_int), ("tile_events", ctypes.c_int)]
+
+
+def _batch_sigs(L):
+    if getattr(L, "_batch_sigs", False):
+        return
+    vp = ctypes.c_void_p
+    L.rv_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64),
+                                  ctypes.POINTER(_BatchOpts), ctypes.POINTER(vp)]
+    L.rv_batch_workspace_size.argtypes = [vp]
+    L.rv_batch_workspace_size.restype = ctypes.c_size_t
+    L.rv_batch_run.argtypes = [vp, vp, vp, vp, ctypes.c_size_t, vp, vp]
+    L.rv_batch_autotune.argtypes = [vp, vp, vp, vp, ctypes.c_size_t, vp, vp, ctypes.POINTER(_BatchOpts)]
+    L.rv_batch_free.argtypes = [vp]
+    L.rv_batch_free.restype = None
+    L._batch_sigs = True
+
+
+class Batch:
+    """Many traces (concatenated, CSR offsets) x nf formulas per trace, run as
+    one captured graph (rv_batch_*)."""
+
+    def __init__(self, formulas, offsets, bucket_records=0, tile_events=0):
+        L = lib()
+        _batch_sigs(L)
+        self.nt = len(formulas)
+        self.nf = len(formulas[0])
+        self._keep = formulas
+        flat = (ctypes.c_void_p * (self.nt * self.nf))(*[f.handle.value for fs in formulas for f in fs])
+        self.offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
+        h = ctypes.c_void_p()
+        opts = _BatchOpts(bucket_records, tile_events)
+        _check(L.rv_batch_create(flat, self.nf, self.nt, self.offsets.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                 ctypes.byref(opts), ctypes.byref(h)))
+        self._h = h
+
+    def workspace_size(self):
+        return int(lib().rv_batch_workspace_size(self._h))
+
+    def run(self, key, pred, ws, dev_results, stream=None):
+        _check(lib().rv_batch_run(self._h, ctypes.c_void_p(key.data_ptr()), ctypes.c_void_p(pred.data_ptr()),
+                                  ctypes.c_void_p(ws.data_ptr()), ws.numel(), ctypes.c_void_p(dev_results.data_ptr()),
+                                  _stream_handle(stream)))
+
+    def autotune(self, key, pred, ws, dev_results, stream=None):
+        ch = _BatchOpts()
+        _check(lib().rv_batch_autotune(self._h, ctypes.c_void_p(key.data_ptr()), ctypes.c_void_p(pred.data_ptr()),
+                                       ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                       ctypes.c_void_p(dev_results.data_ptr()), _stream_handle(stream),
+                                       ctypes.byref(ch)))
+        return {"bucket_records": ch.bucket_records, "tile_events": ch.tile_events}
+
+    def results(self, dev_results):
+        raw = bytes(dev_results.cpu().numpy())
+        return [_result(_Result.from_buffer_copy(raw, i * RESULT_BYTES)) for i in range(self.nt * self.nf)]
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.rv_batch_free(h)
+            self._h = None

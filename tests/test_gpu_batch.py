@@ -1,0 +1,108 @@
+"""GPU parity of the batched path (rv_batch_*): every (trace, formula) result
+equals the CPU oracle and the single-trace launch."""
+import numpy as np
+import pytest
+
+from oracle.verify import Schema, verify as oracle_verify
+from paper_1411_2239_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _formulas(rv, rng, codes, nf):
+    out, texts = [], []
+    while len(out) < nf:
+        body = synth.random_body(rng, codes, depth=int(rng.integers(1, 4)))
+        text = f"{synth.random_quantifier(rng)} x: p(x) => {body}"
+        try:
+            out.append(rv.Formula(text, codes))
+            texts.append(text)
+        except rv.RVError:
+            continue
+    return out, texts
+
+
+def _make(rv, seed, lens, nf):
+    rng = np.random.default_rng(seed)
+    keys, preds, forms, texts, codes_all = [], [], [], [], []
+    for n in lens:
+        nc = int(rng.integers(2, 7))
+        codes = [f"p{j}" for j in range(nc)]
+        nk = max(1, n // 16)
+        keys.append(rng.integers(0, nk, size=n).astype(np.uint32) * np.uint32(2654435761))
+        preds.append(rng.integers(0, nc, size=n).astype(np.uint8))
+        f, t = _formulas(rv, rng, codes, nf)
+        forms.append(f)
+        texts.append(t)
+        codes_all.append(codes)
+    off = np.zeros(len(lens) + 1, dtype=np.uint64)
+    off[1:] = np.cumsum(lens)
+    return keys, preds, forms, texts, codes_all, off
+
+
+def _run(rv, torch, forms, keys, preds, off, **kw):
+    b = rv.Batch(forms, off, **kw)
+    k = torch.from_numpy(np.concatenate(keys).view(np.int32)).cuda()
+    p = torch.from_numpy(np.concatenate(preds)).cuda()
+    ws = torch.empty(b.workspace_size(), dtype=torch.uint8, device="cuda")
+    res = torch.empty(b.nt * b.nf * rv.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    b.run(k, p, ws, res)
+    torch.cuda.synchronize()
+    return b, k, p, ws, res, b.results(res)
+
+
+def test_batch_matches_oracle(rv):
+    import torch
+    lens = [0, 1, 7, 100, 999, 5000, 20000, 64, 3000, 12345]
+    keys, preds, forms, texts, codes, off = _make(rv, 1, lens, 8)
+    _, _, _, _, _, out = _run(rv, torch, forms, keys, preds, off, bucket_records=512)
+    for t in range(len(lens)):
+        for j in range(8):
+            r = out[t * 8 + j]
+            o = oracle_verify(texts[t][j], Schema(codes[t]), keys[t], preds[t])
+            assert r.status == 0
+            assert r.root == o.root and r.root_counts == o.root_counts, (t, j, texts[t][j])
+            assert r.n_nodes[0] == o.n_nodes[0] and r.events == lens[t]
+
+
+def test_batch_matches_single_launch_and_autotune(rv):
+    import torch
+    lens = [int(x) for x in np.exp(np.random.default_rng(2).uniform(np.log(1e3), np.log(3e5), size=12))]
+    keys, preds, forms, texts, codes, off = _make(rv, 2, lens, 32)
+    b, k, p, ws, res, out = _run(rv, torch, forms, keys, preds, off)
+    for t in range(len(lens)):
+        kt = torch.from_numpy(keys[t].view(np.int32)).cuda()
+        pt = torch.from_numpy(preds[t]).cuda()
+        for j in range(0, 32, 5):
+            s = rv.verify(forms[t][j], kt, pt)
+            r = out[t * 32 + j]
+            assert (r.root, r.root_counts, r.n_nodes[0]) == (s.root, s.root_counts, s.n_nodes[0])
+    chosen = b.autotune(k, p, ws, res)
+    assert chosen["bucket_records"] in (1024, 2048, 4096, 8192)
+    b.run(k, p, ws, res)
+    torch.cuda.synchronize()
+    out2 = b.results(res)
+    assert [(r.root, r.root_counts) for r in out2] == [(r.root, r.root_counts) for r in out]
+
+
+def test_batch_bad_predicate(rv):
+    import torch
+    keys, preds, forms, texts, codes, off = _make(rv, 3, [100, 200], 2)
+    preds[1][17] = len(codes[1])          # out of this trace's alphabet
+    _, _, _, _, _, out = _run(rv, torch, forms, keys, preds, off)
+    assert all(r.status == rv.RV_EINVAL for r in out)
+
+
+def test_batch_overfull_bucket_reports_eagain(rv):
+    import torch
+    rng = np.random.default_rng(4)
+    n = 20000
+    keys = [np.arange(n, dtype=np.uint32)]          # every event its own binding
+    preds = [rng.integers(0, 2, size=n).astype(np.uint8)]
+    forms = [[rv.Formula("E x: p(x) => F a", ["a", "b"])]]
+    off = np.array([0, n], dtype=np.uint64)
+    _, _, _, _, _, out = _run(rv, torch, forms, keys, preds, off, bucket_records=8192)
+    assert out[0].status in (rv.RV_OK, rv.RV_EAGAIN)
+    _, _, _, _, _, out = _run(rv, torch, forms, keys, preds, off, bucket_records=256)
+    o = oracle_verify("E x: p(x) => F a", Schema(["a", "b"]), keys[0], preds[0])
+    assert out[0].status == 0 and out[0].root == o.root and out[0].root_counts == o.root_counts
