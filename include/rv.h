@@ -206,6 +206,54 @@ rv_status rv_batch_autotune(rv_batch* b, const uint32_t* key, const uint8_t* pre
                             rv_result* dev_results, cudaStream_t s, rv_batch_opts* chosen);
 void rv_batch_free(rv_batch* b);
 
+/* ------------------------------------------------------------------ online serving
+ * The online mode of Algorithm 1 (Sec. 4.2): repeated invocations on newly
+ * arrived events update the submonitor tree, whose state stays on the GPU.
+ * A service owns one formula (one or two quantifiers; one-quantifier streams
+ * use 32-bit keys, two-quantifier streams 64-bit (d0 << 32) | d1 keys) and up
+ * to max_streams streams, each an independent trace.  Continuous batching: a
+ * push only stages the chunk (host copy) and returns; a worker thread batches
+ * every staged chunk (at most one per stream per batch) onto the GPU while
+ * newer chunks keep arriving.  Every processed chunk yields one
+ * rv_stream_verdict: the stream's six-valued verdict for its whole prefix up to
+ * and including that chunk, and the push -> verdict latency.
+ *   rv_stream_push: chunk arrays are host pointers, copied before return.
+ *     RV_EAGAIN: not admitted (staging budget max_staged_events, or the
+ *     worst case of one new binding per event would exceed max_bindings /
+ *     max_outer); retry later.  RV_EINVAL: closed stream, decreasing ts.
+ *   rv_stream_poll: up to max verdicts in ticket order; waits up to
+ *     timeout_us; RV_ETIMEOUT when none arrived.
+ *   rv_stream_close: drops the stream's queued chunks and verdicts.
+ *   rv_service_close: drains the worker and frees everything (device memory
+ *     through the registered allocator). */
+typedef struct rv_service rv_service;
+typedef struct rv_stream rv_stream;
+typedef struct {
+  uint64_t max_bindings;      /* innermost bindings over all streams (default 2^24) */
+  uint64_t max_outer;         /* outer nodes over all streams (default 2^22) */
+  uint64_t max_batch_events;  /* events per device batch, also the largest chunk (default 2^22) */
+  uint64_t max_staged_events; /* events admitted but not yet processed (default 2^25) */
+  int max_streams;            /* default 64 */
+} rv_service_cfg;
+typedef struct {
+  uint64_t ticket;            /* 1, 2, ... per stream, in push order */
+  int32_t root;               /* rv_verdict of the stream prefix */
+  int32_t status;             /* rv_status of the batch that carried the chunk */
+  uint64_t root_counts[6];
+  uint64_t events;            /* events of the stream up to this chunk */
+  double latency_us;          /* push -> verdict visible to poll */
+} rv_stream_verdict;
+typedef struct {
+  uint64_t batches, admitted, refused, events, bindings, outer_nodes, staged_events;
+} rv_service_counters;
+rv_status rv_service_open(const rv_formula* f, const rv_service_cfg* cfg, rv_service** out);
+rv_status rv_service_close(rv_service* svc);
+rv_status rv_stream_open(rv_service* svc, rv_stream** out);
+rv_status rv_stream_push(rv_stream* st, const rv_trace* chunk, uint64_t* ticket);
+rv_status rv_stream_poll(rv_stream* st, rv_stream_verdict* out, int max, int* n, int timeout_us);
+rv_status rv_stream_close(rv_stream* st);
+rv_status rv_service_stats(rv_service* svc, rv_service_counters* out);
+
 /* ------------------------------------------------------------------ instrumentation
  * The paper times whole monitor runs (Sec. 5.2); these calls time each kernel.
  * rv_profile_enable(1): every kernel launch of the library is bracketed by a

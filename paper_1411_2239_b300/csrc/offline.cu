@@ -435,6 +435,8 @@ struct Params {
   int B1, B2, nq;
   Acc* acc;
   rv_bindings out;
+  int stream_mode;     // 1: fold the batch into StreamState instead of starting from q0
+  StreamState ss;
 };
 
 __device__ __forceinline__ uint64_t key_mult(uint64_t key) { return key * 0x9E3779B97F4A7C15ull; }
@@ -523,13 +525,43 @@ __device__ int outer_slot(OuterTable& U, uint32_t u_local) {
   return -1;
 }
 
+// root counts of a stream move from verdict `from` (0xFF: new node) to `to`
+__device__ __forceinline__ void root_delta(const Params& p, uint32_t stream, uint32_t from, uint32_t to) {
+  if (from == to) return;
+  if (from != 0xFFu) atomicAdd(&p.ss.root[stream * 6 + from], ~0ull);   // -1
+  atomicAdd(&p.ss.root[stream * 6 + to], 1ull);
+}
+
 // verdict of one innermost binding whose composed map over its whole cluster is M
 template <int F>
 __device__ __forceinline__ void finalize_slot(const Params& p, FinalCtx& fc, OuterTable& U, uint64_t skey,
                                               uint64_t M, uint32_t bucket) {
+  const uint32_t b1 = bucket >> p.B2;
+  if (p.stream_mode) {
+    // continue from the binding's stored state; turn a verdict change into deltas
+    const uint32_t b = p.nq == 2 ? (uint32_t)(skey & 0xFFFFFFFFull) : (uint32_t)original_key<F>(skey, b1, p.B1, p.nq);
+    const uint32_t old = p.ss.bstate[b];
+    const bool seen = old & 0x80u;
+    const uint32_t st = seen ? (old & 15u) : (uint32_t)p.tab.q0;
+    const uint32_t ns = (uint32_t)((M >> (4 * st)) & 15ull);
+    const uint32_t v = p.tab.labels[ns];
+    const uint32_t vold = seen ? p.ss.bverdict[b] : 0xFFu;
+    p.ss.bstate[b] = (uint8_t)(0x80u | ns);
+    p.ss.bverdict[b] = (uint8_t)v;
+    if (p.nq <= 1) {
+      root_delta(p, p.ss.bstream[b], vold, v);
+    } else {
+      const int ui = outer_slot(U, (uint32_t)(skey >> 32));
+      if (ui < 0) atomicOr(&p.acc->err, ERR_OUTER_FULL);
+      else if (vold != v) {
+        atomicAdd(&U.ucnt[ui][v], 1u);
+        if (vold != 0xFFu) atomicAdd(&U.ucnt[ui][vold], 0xFFFFFFFFu);   // -1
+      }
+    }
+    return;
+  }
   const uint32_t state = (uint32_t)((M >> (4 * p.tab.q0)) & 15ull);
   const uint32_t v = p.tab.labels[state];
-  const uint32_t b1 = bucket >> p.B2;
   if (p.nq <= 1) {
     fc.h0[v] += 1;
     fc.nodes0 += 1;
@@ -557,6 +589,20 @@ __device__ void finalize_outer(const Params& p, FinalCtx& fc, OuterTable& U, uin
   const uint32_t b1 = bucket >> p.B2;
   for (unsigned int i = threadIdx.x; i < nu; i += blockDim.x) {
     uint64_t v6[6];
+    if (p.stream_mode) {
+      // all bindings of an outer node share this bucket, so this CTA owns the node
+      const uint32_t o = original_outer<F>(U.ukey[i] & 0x7FFFFFFFu, b1, p.B1);
+      for (int v = 0; v < 6; ++v) {
+        const uint32_t c = p.ss.ocounts[(uint64_t)o * 6 + v] + U.ucnt[i][v];
+        p.ss.ocounts[(uint64_t)o * 6 + v] = c;
+        v6[v] = c;
+      }
+      const uint32_t vd = (uint32_t)rvv::valuate(p.tab.q[1].kind, p.tab.q[1].op, p.tab.q[1].num, p.tab.q[1].den, v6);
+      const uint32_t vold = p.ss.overdict[o];
+      p.ss.overdict[o] = (uint8_t)vd;
+      root_delta(p, p.ss.ostream[o], vold, vd);
+      continue;
+    }
     for (int v = 0; v < 6; ++v) v6[v] = U.ucnt[i][v];
     const int vd = rvv::valuate(p.tab.q[1].kind, p.tab.q[1].op, p.tab.q[1].num, p.tab.q[1].den, v6);
     fc.h0[vd] += 1;
@@ -973,7 +1019,7 @@ static MonitorTab make_tab(const rv_formula* f) {
 template <int F>
 static rv_status launch_all(const Plan& pl, const rv_formula* f, const void* key, const uint8_t* pred,
                             const uint32_t* ts, unsigned char* ws, rv_result* dev_out, const rv_bindings* b,
-                            cudaStream_t s) {
+                            cudaStream_t s, const StreamState* ss = nullptr) {
   typedef typename RecT<F>::type Rec;
   Acc* acc = (Acc*)(ws + pl.o_acc);
   RV_CU(cudaMemsetAsync(acc, 0, sizeof(Acc), s));
@@ -985,6 +1031,7 @@ static rv_status launch_all(const Plan& pl, const rv_formula* f, const void* key
   p.nq = f->n_quant;
   p.acc = acc;
   if (b) p.out = *b;
+  if (ss) { p.stream_mode = 1; p.ss = *ss; }
   const uint64_t n = pl.n;
   if (n > 0) {
     uint32_t* hist = (uint32_t*)(ws + pl.o_hist);
@@ -1059,7 +1106,7 @@ static rv_status launch_all(const Plan& pl, const rv_formula* f, const void* key
       std::swap(pin, pout);
     }
   }
-  RV_LAUNCH("k_root", k_root, 1, 32, 0, s, acc, p, n, dev_out);
+  if (!ss) RV_LAUNCH("k_root", k_root, 1, 32, 0, s, acc, p, n, dev_out);
   RV_CU(cudaGetLastError());
   return RV_OK;
 }
@@ -1078,12 +1125,13 @@ static rv_status set_attrs() {
 }
 
 static rv_status dispatch(const Plan& pl, const rv_formula* f, const void* key, const uint8_t* pred, const uint32_t* ts,
-                          unsigned char* ws, rv_result* dev_out, const rv_bindings* b, cudaStream_t s) {
+                          unsigned char* ws, rv_result* dev_out, const rv_bindings* b, cudaStream_t s,
+                          const StreamState* ss = nullptr) {
   rv_status st;
   switch (pl.F) {
-    case FMT_K32: st = set_attrs<FMT_K32>(); if (st) return st; return launch_all<FMT_K32>(pl, f, key, pred, ts, ws, dev_out, b, s);
-    case FMT_K64: st = set_attrs<FMT_K64>(); if (st) return st; return launch_all<FMT_K64>(pl, f, key, pred, ts, ws, dev_out, b, s);
-    default: st = set_attrs<FMT_K2>(); if (st) return st; return launch_all<FMT_K2>(pl, f, key, pred, ts, ws, dev_out, b, s);
+    case FMT_K32: st = set_attrs<FMT_K32>(); if (st) return st; return launch_all<FMT_K32>(pl, f, key, pred, ts, ws, dev_out, b, s, ss);
+    case FMT_K64: st = set_attrs<FMT_K64>(); if (st) return st; return launch_all<FMT_K64>(pl, f, key, pred, ts, ws, dev_out, b, s, ss);
+    default: st = set_attrs<FMT_K2>(); if (st) return st; return launch_all<FMT_K2>(pl, f, key, pred, ts, ws, dev_out, b, s, ss);
   }
 }
 
@@ -1104,6 +1152,28 @@ void rv_dev_free(void* p) {
   if (!p) return;
   if (g_free) g_free(p, g_alloc_ctx);
   else cudaFree(p);
+}
+
+// Streaming: fold one batch whose keys are dense ids (nq == 2: (outer << 32) |
+// binding, 64-bit; nq == 1: binding id as a 64-bit key) into the state ss.
+rv_status rv_offline_stream_batch(const rv_formula* f, const uint64_t* key, const uint8_t* pred, uint64_t n,
+                                  void* ws, size_t ws_bytes, const StreamState* ss, unsigned int* err_out,
+                                  cudaStream_t s) {
+  rv_formula g = *f;
+  g.key_bits = 64;                       // ids are passed as 64-bit keys
+  Plan pl = make_plan(&g, n, 0, nullptr, 0);
+  if (ws_bytes < pl.total) return rv_fail(RV_ENOMEM, "stream workspace of %zu bytes, need %zu", ws_bytes, pl.total);
+  rv_status st = dispatch(pl, &g, key, pred, nullptr, (unsigned char*)ws, nullptr, nullptr, s, ss);
+  if (st) return st;
+  if (err_out && cudaMemcpyAsync(err_out, &((Acc*)((unsigned char*)ws + pl.o_acc))->err, 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return rv_fail(RV_ECUDA, "status copy failed");
+  return RV_OK;
+}
+
+size_t rv_offline_stream_ws(const rv_formula* f, uint64_t n) {
+  rv_formula g = *f;
+  g.key_bits = 64;
+  return make_plan(&g, n, 0, nullptr, 0).total;
 }
 
 extern "C" void rv_set_allocator(rv_alloc_fn alloc, rv_free_fn free_fn, void* ctx) {

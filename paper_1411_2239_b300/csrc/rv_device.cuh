@@ -191,4 +191,18 @@ struct Acc {
   unsigned int next_group[8];   // and of each k_combine level
 };
 
+// ------------------------------------------------------------------ streaming state
+// Device-resident monitor state of the online mode (Sec. 4.2: repeated
+// invocations update the submonitor tree incrementally).  Bindings and outer
+// nodes have dense ids assigned by the streaming pre-pass.
+struct StreamState {
+  uint8_t* bstate;              // [binding] 0x80 | monitor state once seen, 0 before
+  uint8_t* bverdict;            // [binding] last LTL4 verdict
+  uint16_t* bstream;            // [binding] stream (one-quantifier formulas)
+  uint32_t* ocounts;            // [outer][6] child-verdict counts
+  uint8_t* overdict;            // [outer] last verdict, 0xFF before the first
+  uint16_t* ostream;            // [outer] stream
+  unsigned long long* root;     // [stream][6] root child-verdict counts
+};
+
 }  // namespace rvd

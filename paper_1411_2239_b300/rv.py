@@ -341,3 +341,108 @@ class Batch:
         if h is not None and _lib is not None:
             _lib.rv_batch_free(h)
             self._h = None
+
+
+# ---------------------------------------------------------------------- serving
+class _SvcCfg(ctypes.Structure):
+    _fields_ = [("max_bindings", ctypes.c_uint64), ("max_outer", ctypes.c_uint64),
+                ("max_batch_events", ctypes.c_uint64), ("max_staged_events", ctypes.c_uint64),
+                ("max_streams", ctypes.c_int)]
+
+
+class _Verdict(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_uint64), ("root", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("root_counts", ctypes.c_uint64 * 6), ("events", ctypes.c_uint64), ("latency_us", ctypes.c_double)]
+
+
+class _SvcCounters(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in ("batches", "admitted", "refused", "events", "bindings",
+                                              "outer_nodes", "staged_events")]
+
+
+def _svc_sigs(L):
+    if getattr(L, "_svc_sigs", False):
+        return
+    vp = ctypes.c_void_p
+    L.rv_service_open.argtypes = [vp, ctypes.POINTER(_SvcCfg), ctypes.POINTER(vp)]
+    L.rv_service_close.argtypes = [vp]
+    L.rv_stream_open.argtypes = [vp, ctypes.POINTER(vp)]
+    L.rv_stream_push.argtypes = [vp, ctypes.POINTER(_Trace), ctypes.POINTER(ctypes.c_uint64)]
+    L.rv_stream_poll.argtypes = [vp, ctypes.POINTER(_Verdict), ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int]
+    L.rv_stream_close.argtypes = [vp]
+    L.rv_service_stats.argtypes = [vp, ctypes.POINTER(_SvcCounters)]
+    L._svc_sigs = True
+
+
+@dataclass
+class StreamVerdict:
+    ticket: int
+    root: int
+    status: int
+    root_counts: list
+    events: int
+    latency_us: float
+
+
+class Service:
+    """Online verification service (rv_service_*): continuous batching of chunks
+    from many streams, monitor state resident on the GPU."""
+
+    def __init__(self, formula: Formula, max_bindings=0, max_outer=0, max_batch_events=0, max_staged_events=0,
+                 max_streams=0):
+        L = lib()
+        _svc_sigs(L)
+        self.formula = formula
+        cfg = _SvcCfg(max_bindings, max_outer, max_batch_events, max_staged_events, max_streams)
+        h = ctypes.c_void_p()
+        _check(L.rv_service_open(formula.handle, ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+
+    def open_stream(self):
+        h = ctypes.c_void_p()
+        _check(lib().rv_stream_open(self._h, ctypes.byref(h)))
+        return Stream(self, h)
+
+    def stats(self):
+        c = _SvcCounters()
+        _check(lib().rv_service_stats(self._h, ctypes.byref(c)))
+        return {n: getattr(c, n) for n, _ in _SvcCounters._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            lib().rv_service_close(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+
+class Stream:
+    def __init__(self, svc, h):
+        self.svc, self._h = svc, h
+
+    def push(self, key, pred, ts=None):
+        """Stage a chunk (host arrays); returns its ticket; raises RVError(RV_EAGAIN) if not admitted."""
+        key = np.ascontiguousarray(key)
+        pred = np.ascontiguousarray(pred, dtype=np.uint8)
+        tr = _Trace(key.ctypes.data, pred.ctypes.data, None if ts is None else np.ascontiguousarray(ts).ctypes.data,
+                    len(pred))
+        t = ctypes.c_uint64()
+        st = lib().rv_stream_push(self._h, ctypes.byref(tr), ctypes.byref(t))
+        if st != RV_OK:
+            raise RVError(st, last_error())
+        return t.value
+
+    def poll(self, max_n=64, timeout_us=0):
+        buf = (_Verdict * max_n)()
+        n = ctypes.c_int()
+        st = lib().rv_stream_poll(self._h, buf, max_n, ctypes.byref(n), int(timeout_us))
+        if st == RV_ETIMEOUT:
+            return []
+        if st != RV_OK:
+            raise RVError(st, last_error())
+        return [StreamVerdict(v.ticket, v.root, v.status, list(v.root_counts), v.events, v.latency_us)
+                for v in buf[:n.value]]
+
+    def close(self):
+        lib().rv_stream_close(self._h)
