@@ -271,6 +271,24 @@ void rv_profile_enable(int on);
 int rv_profile_collect(rv_kernel_stat* out, int max);
 uint64_t rv_launch_count(void);
 
+/* Offline verification that allocates no device memory (the paper has no
+ * counterpart; this is a convenience of the library).  It is for callers that
+ * cannot allocate when they verify: code running during CUDA graph capture,
+ * where cudaMalloc is not allowed; hosts whose device memory is all owned by
+ * another allocator; monitoring loops that must never block or fail on an
+ * allocation.  Same arguments and result as rv_verify_trace_async (t holds
+ * device arrays, *dev_out is a device struct, work is queued on s), but the
+ * workspace is a fixed 64 MiB array inside the library, which every GPU that
+ * loads librv keeps until the process exits.
+ * Limits: traces of at most 1,000,000 events (and whose workspace fits the
+ * 64 MiB); longer ones return RV_EINVAL with a message, nothing is queued.
+ * The first call on a device looks up the array's device address (set-up,
+ * once per device, with that device current); make that first call before
+ * any stream capture.  All calls share the one array and each call clears
+ * what must start at zero: calls whose work overlaps on the GPU (different
+ * streams, or host threads without ordering) race and give wrong results. */
+rv_status rv_verify_trace_noalloc(const rv_formula* f, const rv_trace* t, rv_result* dev_out, cudaStream_t s);
+
 /* Last error message of the calling thread (never NULL). */
 const char* rv_last_error(void);
 

@@ -1,0 +1,86 @@
+"""GPU test of rv_verify_trace_noalloc, the entry point that allocates nothing.
+
+It exists for callers that cannot allocate device memory while they verify
+(work recorded during CUDA graph capture, hosts whose device memory belongs to
+another allocator, loops that must not block on an allocation).  Its workspace
+is one fixed array inside the library that every call shares, so this test
+calls it several times in a row, on different traces, and checks each result
+against the ordinary entry point rv_verify_trace_async.  Results are integers
+(verdicts and counts), so they must be identical.  The file sorts last so a
+stop-at-first-failure run has already run every other test.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_1411_2239_b300 import rv, synth
+
+pytestmark = pytest.mark.gpu
+
+C1 = "A_{>=0.95} s: socket(s) => G(receive -> F respond)"
+C3 = "A_{>=0.90} u: user(u) => E_{<=3} f: file(u,f) => open && !F close"
+
+
+def _lib():
+    L = rv.lib()
+    L.rv_verify_trace_noalloc.argtypes = [ctypes.c_void_p, ctypes.POINTER(rv._Trace), ctypes.c_void_p,
+                                          ctypes.c_void_p]
+    return L
+
+
+def _dev(torch, a):
+    a = np.ascontiguousarray(a)
+    view = {8: np.int64, 4: np.int32, 1: np.uint8}[a.dtype.itemsize]
+    return torch.from_numpy(a.view(view)).cuda()
+
+
+def _noalloc(torch, f, key, pred):
+    out = torch.zeros(rv.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    tr = rv._Trace(key.data_ptr(), pred.data_ptr(), None, int(pred.shape[0]))
+    st = _lib().rv_verify_trace_noalloc(f.handle, ctypes.byref(tr), ctypes.c_void_p(out.data_ptr()),
+                                        ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    torch.cuda.synchronize()
+    return st, rv.parse_result(bytes(out.cpu().numpy()))
+
+
+def _reference(torch, f, key, pred):
+    n = int(pred.shape[0])
+    ws = torch.empty(rv.workspace_size(f, n), dtype=torch.uint8, device="cuda")
+    out = torch.zeros(rv.RESULT_BYTES, dtype=torch.uint8, device="cuda")
+    rv.verify_async(f, key, pred, ws, out)
+    torch.cuda.synchronize()
+    return rv.parse_result(bytes(out.cpu().numpy()))
+
+
+def _same(a, b):
+    return (a.root, a.status, a.root_counts, a.level_counts, a.n_nodes, a.events) == \
+           (b.root, b.status, b.root_counts, b.level_counts, b.n_nodes, b.events)
+
+
+def test_noalloc_matches_workspace_entry_on_consecutive_calls():
+    import torch
+    t1 = synth.socket_trace(100_000, 1000, n_pending=50, seed=1)
+    t2 = synth.socket_trace(900_000, 20_000, pending_frac=0.03, zipf_s=1.1, seed=2)
+    t3 = synth.file_trace(500_000, 300, 10_000, seed=3)
+    f1 = rv.Formula(C1, t1.codes)
+    f3 = rv.Formula(C3, t3.codes, key_bits=64)
+    cases = [(f1, t1), (f1, t2), (f3, t3), (f1, t1), (f3, t3)]   # repeated calls share the scratch array
+    for f, t in cases:
+        key, pred = _dev(torch, t.key), _dev(torch, t.pred)
+        st, got = _noalloc(torch, f, key, pred)
+        assert st == rv.RV_OK, rv.last_error()
+        want = _reference(torch, f, key, pred)
+        assert want.status == 0
+        assert _same(got, want), (got, want)
+
+
+def test_noalloc_rejects_traces_over_the_limit():
+    import torch
+    f = rv.Formula(C1, synth.SOCKET_CODES)
+    n = 1_000_001
+    key = torch.zeros(n, dtype=torch.int32, device="cuda")
+    pred = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    st, _ = _noalloc(torch, f, key, pred)
+    assert st == rv.RV_EINVAL
+    assert "1000000" in rv.last_error()
