@@ -680,6 +680,8 @@ extern "C" rv_status rv_batch_run(rv_batch* b, const uint32_t* key, const uint8_
     BCU(cudaFuncSetAttribute(k_bfold, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BFoldShared)));
     g_bfold_attr = true;
   }
+  if (rv_prof_enabled())   // per-kernel events need eager launches, not a graph replay
+    return enqueue(b, key, pred, (unsigned char*)ws, dev_results, s);
   if (!b->exec || b->g_key != key || b->g_pred != pred || b->g_ws != ws || b->g_res != dev_results) {
     if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
     if (!b->cap) BCU(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));

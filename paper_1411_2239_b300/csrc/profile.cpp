@@ -45,6 +45,8 @@ void rv_prof_end(cudaStream_t s) {
   t_begin = nullptr;
 }
 
+bool rv_prof_enabled() { return g_on; }
+
 void rv_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 extern "C" void rv_profile_enable(int on) {

@@ -6,6 +6,7 @@
 void rv_prof_begin(const char* name, cudaStream_t s);
 void rv_prof_end(cudaStream_t s);
 void rv_count_launch();
+bool rv_prof_enabled();
 
 #define RV_LAUNCH(name, kernel, grid, block, smem, stream, ...)   \
   do {                                                            \
