@@ -50,11 +50,11 @@ constexpr int TILE2 = 8192;
 constexpr int COLCHUNK = 64;
 constexpr uint16_t NO_SLOT = 0xFFFF;
 constexpr uint16_t FULL_SLOT = 0xFFFE;
+constexpr uint16_t DOM_SLOT = 0xFFFD;   // record of the unit's dominant-candidate key
 constexpr uint64_t EMPTY_KEY = ~0ull;
 constexpr unsigned FULL = 0xFFFFFFFFu;
 constexpr int SPIN_LIMIT = 1 << 22;
 constexpr int BATCH = 16;      // rounds of 32 events whose loads are issued together
-constexpr int FBATCH = 8;      // the same for the fold
 
 struct Tile { uint32_t bucket, k, K, pad; uint64_t begin, end; };
 struct Item { uint64_t off; uint32_t cnt, pad; };
@@ -75,6 +75,17 @@ __device__ __forceinline__ uint32_t match_bits(uint32_t v, bool valid) {
   uint32_t m = valid ? vb : ~vb;
 #pragma unroll
   for (int k = 0; k < BITS; ++k) {
+    const uint32_t bk = __ballot_sync(FULL, (v >> k) & 1u);
+    m &= ((v >> k) & 1u) ? bk : ~bk;
+  }
+  return m;
+}
+
+// the same with a runtime number of bits (values below 2^nbits)
+__device__ __forceinline__ uint32_t match_nbits(uint32_t v, bool valid, int nbits) {
+  const uint32_t vb = __ballot_sync(FULL, valid);
+  uint32_t m = valid ? vb : ~vb;
+  for (int k = 0; k < nbits; ++k) {
     const uint32_t bk = __ballot_sync(FULL, (v >> k) & 1u);
     m &= ((v >> k) & 1u) ? bk : ~bk;
   }
@@ -124,6 +135,141 @@ k_hist(const void* keyp, const uint32_t* ts, uint64_t n, uint64_t per_warp, int 
   }
   if (__any_sync(FULL, bad_ts) && lane == 0) atomicOr(&acc->err, ERR_TS);
   for (int b = lane; b < P; b += 32) hist[(uint64_t)gw * P + b] = cnt[b];
+}
+
+// ------------------------------------------------------------------ level-1 multisplit, CTA tiles
+// With 256 first-level buckets a CTA splits a tile of TILE events at a time:
+// the tile is counting-sorted by bucket in shared memory (stable: per-warp
+// counts over contiguous slices) and each bucket's run is written out
+// contiguously, so the global writes are runs rather than scattered words.
+template <int F> struct TileSize { static constexpr int v = 4096; };
+template <> struct TileSize<FMT_K32> { static constexpr int v = 8192; };
+constexpr int TB_THREADS = 256;
+constexpr int TB_WARPS = TB_THREADS / 32;
+
+template <int F>
+__global__ void __launch_bounds__(TB_THREADS)
+k_hist_tile(const void* keyp, const uint32_t* ts, uint64_t n, int nq, uint32_t* hist, Acc* acc) {
+  constexpr int T = TileSize<F>::v;
+  __shared__ uint32_t cnt[256];
+  const uint64_t begin = (uint64_t)blockIdx.x * T;
+  const int len = (int)min((uint64_t)T, n - begin);
+  cnt[threadIdx.x] = 0;
+  __syncthreads();
+  bool bad_ts = false;
+  for (int i0 = threadIdx.x; i0 < len; i0 += TB_THREADS * BATCH) {
+    uint32_t b[BATCH];
+#pragma unroll
+    for (int j = 0; j < BATCH; ++j) {
+      const int i = i0 + j * TB_THREADS;
+      b[j] = i < len ? make_record<F>(load_key<F>(keyp, begin + i), 0, 8, nq).bucket : 0xFFFFFFFFu;
+    }
+#pragma unroll
+    for (int j = 0; j < BATCH; ++j) {
+      const int i = i0 + j * TB_THREADS;
+      if (b[j] != 0xFFFFFFFFu) {
+        atomicAdd(&cnt[b[j]], 1u);
+        if (ts && begin + i > 0 && ts[begin + i] < ts[begin + i - 1]) bad_ts = true;
+      }
+    }
+  }
+  if (__syncthreads_or(bad_ts) && threadIdx.x == 0) atomicOr(&acc->err, ERR_TS);
+  hist[(uint64_t)blockIdx.x * 256 + threadIdx.x] = cnt[threadIdx.x];
+}
+
+template <int F>
+struct TileShared {
+  typename RecT<F>::type srec[TileSize<F>::v];
+  typename RecT<F>::type orec[TileSize<F>::v];
+  uint8_t sb[TileSize<F>::v];
+  uint8_t ob[TileSize<F>::v];
+  uint32_t wcur[TB_WARPS][256];
+  uint32_t loc[256];
+  uint64_t gbase[256];
+  uint32_t tsum[TB_WARPS];
+};
+
+template <int F>
+__global__ void __launch_bounds__(TB_THREADS)
+k_scatter_tile(const void* keyp, const uint8_t* pred, uint64_t n, int nq, int n_letters, const uint32_t* pre,
+               const uint64_t* bstart, typename RecT<F>::type* out, Acc* acc) {
+  typedef typename RecT<F>::type Rec;
+  constexpr int T = TileSize<F>::v;
+  extern __shared__ __align__(16) unsigned char tile_smem[];
+  TileShared<F>& S = *reinterpret_cast<TileShared<F>*>(tile_smem);
+  const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t lt = lanemask_lt();
+  const uint64_t begin = (uint64_t)blockIdx.x * T;
+  const int len = (int)min((uint64_t)T, n - begin);
+  for (int i = threadIdx.x; i < TB_WARPS * 256; i += TB_THREADS) S.wcur[i / 256][i % 256] = 0;
+  bool bad = false;
+  // 1. records and buckets of the tile, in trace order
+  for (int i0 = threadIdx.x; i0 < len; i0 += TB_THREADS * BATCH) {
+    uint64_t k[BATCH];
+    uint32_t l[BATCH];
+#pragma unroll
+    for (int j = 0; j < BATCH; ++j) {
+      const int i = i0 + j * TB_THREADS;
+      k[j] = i < len ? load_key<F>(keyp, begin + i) : 0;
+      l[j] = i < len ? pred[begin + i] : 0;
+    }
+#pragma unroll
+    for (int j = 0; j < BATCH; ++j) {
+      const int i = i0 + j * TB_THREADS;
+      if (i < len) {
+        uint32_t letter = l[j];
+        if (letter >= (uint32_t)n_letters) { bad = true; letter = 0; }
+        const Bucketed r = make_record<F>(k[j], letter, 8, nq);
+        S.srec[i] = (Rec)r.rec;
+        S.sb[i] = (uint8_t)r.bucket;
+      }
+    }
+  }
+  __syncthreads();
+  // 2. per-warp counts over contiguous slices
+  const int per = (len + TB_WARPS - 1) / TB_WARPS;
+  const int w0 = min(len, wl * per), w1 = min(len, w0 + per);
+  for (int i = w0 + lane; i < w1; i += 32) atomicAdd(&S.wcur[wl][S.sb[i]], 1u);
+  __syncthreads();
+  // 3. thread b: offsets of bucket b inside the tile and in the output
+  {
+    const int b = threadIdx.x;
+    uint32_t tot = 0;
+    for (int w = 0; w < TB_WARPS; ++w) tot += S.wcur[w][b];
+    uint32_t x = tot;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(FULL, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) S.tsum[wl] = x;
+    __syncthreads();
+    uint32_t run = x - tot;
+    for (int w = 0; w < wl; ++w) run += S.tsum[w];
+    S.loc[b] = run;
+    S.gbase[b] = bstart[b] + pre[(uint64_t)blockIdx.x * 256 + b];
+    for (int w = 0; w < TB_WARPS; ++w) { const uint32_t c = S.wcur[w][b]; S.wcur[w][b] = run; run += c; }
+  }
+  __syncthreads();
+  // 4. stable placement by bucket
+  for (int base = w0; base < w1; base += 32) {
+    const int i = base + lane;
+    const bool v = i < w1;
+    const uint32_t b = v ? S.sb[i] : 0u;
+    const uint32_t peers = match_bits<8>(b, v);
+    uint32_t pos = 0;
+    if (v) pos = S.wcur[wl][b] + __popc(peers & lt);
+    __syncwarp();
+    if (v && lane == __ffs(peers) - 1) S.wcur[wl][b] += __popc(peers);
+    __syncwarp();
+    if (v) { S.orec[pos] = S.srec[i]; S.ob[pos] = (uint8_t)b; }
+  }
+  __syncthreads();
+  // 5. runs of each bucket go out contiguously
+  for (int i = threadIdx.x; i < len; i += TB_THREADS) {
+    const uint32_t b = S.ob[i];
+    out[S.gbase[b] + (i - S.loc[b])] = S.orec[i];
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&acc->err, ERR_LETTER);
 }
 
 // per (bucket, chunk of warps): chunk sums
@@ -430,6 +576,12 @@ struct FinalCtx {              // per-thread tallies, reduced once per CTA
   uint32_t nodes0, nodes1;
 };
 
+// h[v] += 1 with compile-time indices, so the tallies stay in registers
+__device__ __forceinline__ void inc6(uint32_t* h, uint32_t v) {
+#pragma unroll
+  for (int k = 0; k < 6; ++k) h[k] += v == (uint32_t)k;
+}
+
 struct Params {
   MonitorTab tab;
   int B1, B2, nq;
@@ -563,10 +715,10 @@ __device__ __forceinline__ void finalize_slot(const Params& p, FinalCtx& fc, Out
   const uint32_t state = (uint32_t)((M >> (4 * p.tab.q0)) & 15ull);
   const uint32_t v = p.tab.labels[state];
   if (p.nq <= 1) {
-    fc.h0[v] += 1;
+    inc6(fc.h0, v);
     fc.nodes0 += 1;
   } else {
-    fc.h1[v] += 1;
+    inc6(fc.h1, v);
     fc.nodes1 += 1;
     int ui = outer_slot(U, (uint32_t)(skey >> 32));
     if (ui < 0) atomicOr(&p.acc->err, ERR_OUTER_FULL);
@@ -605,7 +757,7 @@ __device__ void finalize_outer(const Params& p, FinalCtx& fc, OuterTable& U, uin
     }
     for (int v = 0; v < 6; ++v) v6[v] = U.ucnt[i][v];
     const int vd = rvv::valuate(p.tab.q[1].kind, p.tab.q[1].op, p.tab.q[1].num, p.tab.q[1].den, v6);
-    fc.h0[vd] += 1;
+    inc6(fc.h0, (uint32_t)vd);
     fc.nodes0 += 1;
     if (p.out.outer_keys) {
       unsigned long long idx = atomicAdd(&p.acc->n_out_outer, 1ull);
@@ -639,27 +791,44 @@ __device__ __forceinline__ void clear_final(FinalCtx& fc) {
 }
 
 // ------------------------------------------------------------------ fold
+constexpr int UNIT_MAX = 8192;     // records of one unit held in shared memory
+
 struct FoldShared {
   uint64_t lmap[RV_MAX_LETTERS];
-  uint64_t wmap[FOLD_WARPS][SLOTS];
   SlotTable T;
   OuterTable U;
+  uint8_t letter[UNIT_MAX];
+  uint16_t slot_of[UNIT_MAX];          // NO_SLOT: record outside the current pass
+  uint8_t sorted[UNIT_MAX];            // letters grouped by slot, trace order kept
+  uint32_t wcnt[FOLD_WARPS][SLOTS / 2];  // two 16-bit per-warp counters (then cursors) per word
+  uint32_t seg[SLOTS + 1];
+  uint32_t tsum[FOLD_WARPS];
+  uint64_t firstmap[FOLD_THREADS];     // map of a piece's first run when that run began earlier
+  uint64_t lastval[FOLD_THREADS];      // state or map of a piece's last run when it goes on
+  uint64_t wmaps[FOLD_WARPS];
+  int dom;                             // 1 when slot 0 is the dominant candidate in this pass
   uint32_t pass_bits[64], pass_val[64];
   int npass;
   uint64_t item_off;
   uint32_t item_cnt;
 };
 
+__device__ __forceinline__ uint32_t wc_get(const uint32_t* row, uint32_t s) { return (row[s >> 1] >> (16 * (s & 1))) & 0xFFFFu; }
+
+// Fold of one unit: (1) slot of every record, (2) stable counting sort of the
+// unit's letters by slot (per-warp counts over contiguous slices), (3) each
+// binding's run of letters is folded -- short runs by one thread, long runs by
+// a warp composing per-lane maps and combining them in lane order.
 template <int F>
 __global__ void __launch_bounds__(FOLD_THREADS, 2)
 k_fold(const typename RecT<F>::type* recs, const Tile* units, const unsigned int* n_units, Params p,
        Item* items, Pair* pool) {
   extern __shared__ __align__(16) unsigned char fold_smem[];
   FoldShared& S = *reinterpret_cast<FoldShared*>(fold_smem);
-  const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31, nthr = FOLD_THREADS;
   const int ns = p.tab.n_states;
   const uint32_t lt = lanemask_lt();
-  for (int i = threadIdx.x; i < RV_MAX_LETTERS; i += blockDim.x) S.lmap[i] = p.tab.maps[i];
+  for (int i = threadIdx.x; i < RV_MAX_LETTERS; i += nthr) S.lmap[i] = p.tab.maps[i];
   FinalCtx fc;
   clear_final(fc);
   __shared__ unsigned int s_next;
@@ -672,72 +841,59 @@ k_fold(const typename RecT<F>::type* recs, const Tile* units, const unsigned int
     if (u >= nun) break;
     const Tile t = units[u];
     const bool single = t.K == 1;
-    const uint64_t len = t.end - t.begin;
-    const uint64_t chunk = (len + FOLD_WARPS - 1) / FOLD_WARPS;
-    const uint64_t wbeg = t.begin + min(len, chunk * wl), wend = t.begin + min(len, chunk * (wl + 1));
-    __syncthreads();
+    const bool use_state = single && !p.stream_mode;   // a single unit starting at q0: plain states
+    const int len = (int)(t.end - t.begin);            // <= UNIT_MAX by construction
     if (threadIdx.x == 0) {
       S.npass = 1; S.pass_bits[0] = 0; S.pass_val[0] = 0;
       S.item_cnt = 0;
       S.item_off = single ? 0 : atomicAdd(&p.acc->pair_top[0], (unsigned long long)len);
     }
     if (t.k == 0) reset_outer(S.U);
-    __syncthreads();
+    const int per = (len + FOLD_WARPS - 1) / FOLD_WARPS;
+    const int w0 = min(len, wl * per), w1 = min(len, w0 + per);
     while (true) {
       __syncthreads();
       if (S.npass == 0) break;
       const int bits = (int)S.pass_bits[S.npass - 1];
       const uint32_t val = S.pass_val[S.npass - 1];
+      // The key of the unit's first record is the dominant candidate: under a
+      // Zipf law one key fills most records of a heavy unit.  It takes slot 0
+      // and its records skip hashing and sorting (folded in place below).
+      const uint64_t cand = (uint64_t)recs[t.begin] >> 8;
+      const bool dom = in_pass(cand, bits, val);
       reset_table(S.T);
       __syncthreads();
-      for (uint64_t base0 = wbeg; base0 < wend; base0 += 32 * FBATCH) {
-        uint64_t rb[FBATCH];
+      if (threadIdx.x == 0 && dom) find_or_insert(S.T, cand, p.acc, [](unsigned int) {});
+      __syncthreads();
+      // 1. letters and binding slots; RB records per thread are loaded together
+      constexpr int RB = 16;
+      for (int i0 = threadIdx.x; i0 < len; i0 += nthr * RB) {
+        uint64_t r[RB];
 #pragma unroll
-        for (int j = 0; j < FBATCH; ++j) {
-          const uint64_t i = base0 + j * 32 + lane;
-          rb[j] = i < wend ? (uint64_t)recs[i] : 0;
+        for (int j = 0; j < RB; ++j) {
+          const int i = i0 + j * nthr;
+          r[j] = i < len ? (uint64_t)recs[t.begin + i] : 0ull;
         }
 #pragma unroll
-        for (int j = 0; j < FBATCH; ++j) {
-          const uint64_t rec = rb[j];
-          const bool v = base0 + j * 32 + lane < wend;
-          const uint64_t key = rec >> 8;
-          int slot = -1;
-          if (v && in_pass(key, bits, val)) {
-            slot = find_or_insert(S.T, key, p.acc, [&](unsigned int s) {
-              for (int w = 0; w < FOLD_WARPS; ++w) S.wmap[w][s] = IDENTITY_MAP;
-            });
+        for (int j = 0; j < RB; ++j) {
+          const int i = i0 + j * nthr;
+          if (i < len) {
+            const uint64_t key = r[j] >> 8;
+            uint16_t slv = NO_SLOT;
+            if (dom && key == cand) {
+              slv = DOM_SLOT;
+            } else if (in_pass(key, bits, val)) {
+              const int sl = find_or_insert(S.T, key, p.acc, [](unsigned int) {});
+              if (sl >= 0) slv = (uint16_t)sl;
+            }
+            S.slot_of[i] = slv;
+            S.letter[i] = (uint8_t)(r[j] & 0xFF);
           }
-          // ordered composition of the letters of equal slots in this round:
-          // a tree over ranks inside each group (rank r absorbs rank r+s)
-          const bool valid = slot >= 0;
-          const uint32_t peers = match_bits<10>((uint32_t)slot, valid);
-          const int r = __popc(peers & lt), g = __popc(peers);
-          uint64_t M = valid ? S.lmap[rec & 0xFF] : IDENTITY_MAP;
-          const unsigned gmax = __reduce_max_sync(FULL, valid ? (unsigned)g : 1u);
-          // nxt: lane of rank r + st in my group (pointer doubling), -1 if none
-          int nxt = -1;
-          if (gmax > 1 && valid) {
-            const uint32_t above = peers & ~((2u << lane) - 1u);
-            nxt = above ? __ffs(above) - 1 : -1;
-          }
-          for (int st = 1; st < (int)gmax; st <<= 1) {
-            const bool take = valid && (r & (2 * st - 1)) == 0 && nxt >= 0;
-            const int src = nxt >= 0 ? nxt : lane;
-            const uint64_t o = __shfl_sync(FULL, M, src);
-            const int n2 = __shfl_sync(FULL, nxt, src);
-            if (take) M = apply_map(M, o, ns);
-            nxt = nxt >= 0 ? n2 : -1;
-          }
-          if (valid && r == 0) S.wmap[wl][slot] = apply_map(S.wmap[wl][slot], M, ns);
-          __syncwarp();
         }
       }
       __syncthreads();
       if (S.T.ovf) {
-        __syncthreads();
         if (threadIdx.x == 0) {
-          // split this pass into two halves on one more key bit
           S.npass -= 1;
           if (bits >= 20 || S.npass + 2 > 64) {
             atomicOr(&p.acc->err, ERR_SPIN);
@@ -750,15 +906,159 @@ k_fold(const typename RecT<F>::type* recs, const Tile* units, const unsigned int
         }
         continue;
       }
-      const unsigned int nsl = min(S.T.nslots, (unsigned int)SLOTS);
-      for (unsigned int s = threadIdx.x; s < nsl; s += blockDim.x) {
-        uint64_t M = S.wmap[0][s];
-        for (int w = 1; w < FOLD_WARPS; ++w) M = apply_map(M, S.wmap[w][s], ns);
-        if (single) finalize_slot<F>(p, fc, S.U, S.T.skey[s], M, t.bucket);
-        else pool[S.item_off + S.item_cnt + s] = Pair{S.T.skey[s], M};
+      const int nsl = (int)min(S.T.nslots, (unsigned int)SLOTS);
+      const int nw = (nsl + 1) / 2;                        // counter words in use per warp
+      const int nbits = nsl > 1 ? 32 - __clz(nsl - 1) : 1;
+      for (int i = threadIdx.x; i < FOLD_WARPS * nw; i += nthr) S.wcnt[i / nw][i % nw] = 0;
+      __syncthreads();
+      // 2. per-warp counts, then an exclusive scan over (slot, warp)
+      for (int i = w0 + lane; i < w1; i += 32) {
+        const uint32_t sl = S.slot_of[i];
+        if (sl < (uint32_t)SLOTS) atomicAdd(&S.wcnt[wl][sl >> 1], 1u << (16 * (sl & 1)));
       }
       __syncthreads();
-      if (threadIdx.x == 0) { S.item_cnt += nsl; S.npass -= 1; }
+      {
+        // thread t owns slot pairs 2t+2k*nthr ... (pairs share a counter word)
+        const int np = nw;                     // slot pairs in use
+        const int pairs_per = (np + nthr - 1) / nthr;
+        const int p0 = min(np, threadIdx.x * pairs_per), p1 = min(np, p0 + pairs_per);
+        uint32_t sum = 0;
+        for (int q = p0; q < p1; ++q)
+          for (int w = 0; w < FOLD_WARPS; ++w) { const uint32_t word = S.wcnt[w][q]; sum += (word & 0xFFFFu) + (word >> 16); }
+        uint32_t x = sum;
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(FULL, x, o);
+          if (lane >= o) x += y;
+        }
+        if (lane == 31) S.tsum[wl] = x;
+        __syncthreads();
+        uint32_t run = x - sum;
+        for (int w = 0; w < wl; ++w) run += S.tsum[w];
+        for (int q = p0; q < p1; ++q) {
+          uint32_t t0 = 0, t1 = 0;
+          for (int w = 0; w < FOLD_WARPS; ++w) { const uint32_t word = S.wcnt[w][q]; t0 += word & 0xFFFFu; t1 += word >> 16; }
+          S.seg[2 * q] = run;
+          S.seg[2 * q + 1] = run + t0;
+          uint32_t c0 = run, c1 = run + t0;
+          for (int w = 0; w < FOLD_WARPS; ++w) {
+            const uint32_t word = S.wcnt[w][q];
+            S.wcnt[w][q] = (c0 & 0xFFFFu) | ((c1 & 0xFFFFu) << 16);
+            c0 += word & 0xFFFFu;
+            c1 += word >> 16;
+          }
+          run += t0 + t1;
+        }
+        if (threadIdx.x == nthr - 1) S.seg[nsl] = run;   // total placed in this pass
+      }
+      __syncthreads();
+      // stable placement: each warp walks its slice in order
+      for (int base = w0; base < w1; base += 32) {
+        const int i = base + lane;
+        const uint32_t sl = i < w1 ? S.slot_of[i] : (uint32_t)NO_SLOT;
+        const bool v = sl < (uint32_t)SLOTS;
+        const uint32_t peers = match_nbits(v ? sl : 0u, v, nbits);
+        uint32_t pos = 0;
+        if (v) pos = wc_get(S.wcnt[wl], sl) + __popc(peers & lt);
+        __syncwarp();
+        if (v && lane == __ffs(peers) - 1) atomicAdd(&S.wcnt[wl][sl >> 1], (uint32_t)__popc(peers) << (16 * (sl & 1)));
+        __syncwarp();
+        if (v) S.sorted[pos] = S.letter[i];
+      }
+      __syncthreads();
+      // 3. runs: every thread folds an equal piece of the sorted letters; a run
+      // inside one piece is finished there, a run across pieces is joined below
+      const uint32_t TOT = S.seg[nsl];
+      const uint32_t C = (TOT + nthr - 1) / nthr;
+      const uint32_t pa = min(TOT, threadIdx.x * C), pz = min(TOT, pa + C);
+      if (pa < pz) {
+        int lo = 0, hi = nsl - 1;                 // run containing position pa
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (S.seg[mid] <= pa) lo = mid; else hi = mid - 1;
+        }
+        int sl = lo;
+        uint32_t pos = pa;
+        while (pos < pz) {
+          const uint32_t rs = S.seg[sl], re = S.seg[sl + 1];
+          const uint32_t end = min(pz, re);
+          if (end > pos) {
+            const bool starts = pos == rs, ends = end == re;
+            uint64_t V;
+            if (use_state && starts) {
+              uint32_t st = (uint32_t)p.tab.q0;
+              for (uint32_t j = pos; j < end; ++j) st = step_state(st, S.lmap[S.sorted[j]]);
+              V = (uint64_t)st << (4 * p.tab.q0);   // nibble q0 carries the state
+            } else {
+              V = IDENTITY_MAP;
+              for (uint32_t j = pos; j < end; ++j) V = apply_map(V, S.lmap[S.sorted[j]], ns);
+            }
+            if (starts && ends) {
+              if (single) finalize_slot<F>(p, fc, S.U, S.T.skey[sl], V, t.bucket);
+              else pool[S.item_off + S.item_cnt + sl] = Pair{S.T.skey[sl], V};
+            } else if (!starts) {
+              S.firstmap[threadIdx.x] = V;          // continues a run begun in an earlier piece
+            } else {
+              S.lastval[threadIdx.x] = V;           // begins a run that goes on
+            }
+          }
+          pos = end;
+          ++sl;
+        }
+      }
+      __syncthreads();
+      // join runs that cross pieces: the piece where a run begins composes the
+      // first-run maps of the following pieces in order
+      if (pa < pz) {
+        int sl = nsl - 1;
+        {
+          int lo = 0, hi = nsl - 1;               // run containing position pz - 1
+          while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (S.seg[mid] <= pz - 1) lo = mid; else hi = mid - 1;
+          }
+          sl = lo;
+        }
+        const uint32_t rs = S.seg[sl], re = S.seg[sl + 1];
+        if (re > pz && rs >= pa) {                // my last run begins here and goes on
+          uint64_t V = S.lastval[threadIdx.x];
+          const bool st_mode = use_state;          // V holds a state at nibble q0
+          for (uint32_t q = threadIdx.x + 1; q < (uint32_t)nthr && q * C < re; ++q) {
+            const uint64_t Mq = S.firstmap[q];
+            if (st_mode) {
+              const uint32_t st = step_state((uint32_t)((V >> (4 * p.tab.q0)) & 15ull), Mq);
+              V = (uint64_t)st << (4 * p.tab.q0);
+            } else {
+              V = apply_map(V, Mq, ns);
+            }
+          }
+          if (single) finalize_slot<F>(p, fc, S.U, S.T.skey[sl], V, t.bucket);
+          else pool[S.item_off + S.item_cnt + sl] = Pair{S.T.skey[sl], V};
+        }
+      }
+      __syncthreads();
+      // the dominant candidate (slot 0): each thread folds its contiguous piece
+      // of the unit in trace order, pieces are combined in order
+      if (dom) {
+        const int c = (len + nthr - 1) / nthr;
+        const int a = min(len, (int)threadIdx.x * c), z = min(len, a + c);
+        uint64_t M = IDENTITY_MAP;
+        for (int i = a; i < z; ++i)
+          if (S.slot_of[i] == DOM_SLOT) M = apply_map(M, S.lmap[S.letter[i]], ns);
+        for (int off = 1; off < 32; off <<= 1) {
+          const uint64_t o = __shfl_down_sync(FULL, M, off);
+          if ((lane & (2 * off - 1)) == 0) M = apply_map(M, o, ns);
+        }
+        if (lane == 0) S.wmaps[wl] = M;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          uint64_t T = S.wmaps[0];
+          for (int w = 1; w < FOLD_WARPS; ++w) T = apply_map(T, S.wmaps[w], ns);
+          if (single) finalize_slot<F>(p, fc, S.U, S.T.skey[0], T, t.bucket);
+          else pool[S.item_off + S.item_cnt + 0] = Pair{S.T.skey[0], T};
+        }
+        __syncthreads();
+      }
+      if (threadIdx.x == 0) { S.item_cnt += (uint32_t)nsl; S.npass -= 1; }
     }
     __syncthreads();
     if (single) finalize_outer<F>(p, fc, S.U, t.bucket);
@@ -908,6 +1208,7 @@ __global__ void k_root(const Acc* acc, Params p, uint64_t n, rv_result* out) {
 // ------------------------------------------------------------------ host side
 struct Plan {
   int F, B1, B2, P1, P, G_w, nchunk;
+  bool tiled;
   uint64_t n, per_warp, unit;
   uint64_t max_tiles2, max_units;
   int levels;
@@ -946,7 +1247,8 @@ static Plan make_plan(const rv_formula* f, uint64_t n, int host_input, const rv_
   pl.B2 = std::min(7, std::max(0, b2));
   pl.P = pl.P1 << pl.B2;
   pl.unit = o && o->unit_records ? (uint64_t)o->unit_records : 8192;
-  pl.unit = std::max<uint64_t>(256, pl.unit);
+  pl.unit = std::min<uint64_t>(UNIT_MAX, std::max<uint64_t>(256, pl.unit));
+  pl.tiled = pl.B1 == 8;
   const uint64_t max_w = (uint64_t)num_sms() * 3 * SC_WARPS;
   uint64_t gw = (n + 2047) / 2048;
   if (gw > max_w) gw = max_w;
@@ -955,6 +1257,10 @@ static Plan make_plan(const rv_formula* f, uint64_t n, int host_input, const rv_
   if (pl.per_warp == 0) pl.per_warp = 32;
   pl.G_w = (int)((n + pl.per_warp - 1) / pl.per_warp);
   if (pl.G_w < 1) pl.G_w = 1;
+  if (pl.tiled) {   // one row of the bucket histogram per CTA tile
+    pl.per_warp = pl.F == FMT_K32 ? TileSize<FMT_K32>::v : TileSize<FMT_K64>::v;
+    pl.G_w = (int)std::max<uint64_t>(1, (n + pl.per_warp - 1) / pl.per_warp);
+  }
   pl.nchunk = (pl.G_w + COLCHUNK - 1) / COLCHUNK;
   pl.max_tiles2 = n / TILE2 + pl.P1 + 1;
   pl.max_units = n / pl.unit + pl.P + 1;
@@ -1041,14 +1347,21 @@ static rv_status launch_all(const Plan& pl, const rv_formula* f, const void* key
     Rec* recA = (Rec*)(ws + pl.o_recA);
     const int sc_blocks = (pl.G_w + SC_WARPS - 1) / SC_WARPS;
     const size_t sc_smem = (size_t)SC_WARPS * pl.P1 * 4;
-    RV_LAUNCH("k_hist", k_hist<F>, sc_blocks, SC_WARPS * 32, sc_smem, s, key, ts, n, pl.per_warp, pl.G_w, pl.B1, f->n_quant, hist, acc);
+    if (pl.tiled)
+      RV_LAUNCH("k_hist_tile", k_hist_tile<F>, pl.G_w, TB_THREADS, 0, s, key, ts, n, f->n_quant, hist, acc);
+    else
+      RV_LAUNCH("k_hist", k_hist<F>, sc_blocks, SC_WARPS * 32, sc_smem, s, key, ts, n, pl.per_warp, pl.G_w, pl.B1, f->n_quant, hist, acc);
     const int ct = pl.P1 * pl.nchunk;
     RV_LAUNCH("k_colscan_a", k_colscan_a, (ct + 255) / 256, 256, 0, s, hist, pl.G_w, pl.P1, pl.nchunk, part);
     RV_LAUNCH("k_colscan_b", k_colscan_b, (pl.P1 + 255) / 256, 256, 0, s, part, pl.P1, pl.nchunk, tot1);
     RV_LAUNCH("k_colscan_c", k_colscan_c, (ct + 255) / 256, 256, 0, s, hist, pl.G_w, pl.P1, pl.nchunk, part);
     RV_LAUNCH("k_bucket_scan", k_bucket_scan, 1, 1024, 0, s, tot1, pl.P1, bstart1);
-    RV_LAUNCH("k_scatter", k_scatter<F>, sc_blocks, SC_WARPS * 32, sc_smem, s, key, pred, n, pl.per_warp, pl.G_w, pl.B1, f->n_quant,
-                                                          f->n_letters, hist, bstart1, recA, acc);
+    if (pl.tiled)
+      RV_LAUNCH("k_scatter_tile", k_scatter_tile<F>, pl.G_w, TB_THREADS, sizeof(TileShared<F>), s, key, pred, n,
+                f->n_quant, f->n_letters, hist, bstart1, recA, acc);
+    else
+      RV_LAUNCH("k_scatter", k_scatter<F>, sc_blocks, SC_WARPS * 32, sc_smem, s, key, pred, n, pl.per_warp, pl.G_w, pl.B1, f->n_quant,
+                f->n_letters, hist, bstart1, recA, acc);
     Rec* recs = recA;
     uint64_t* bstart = bstart1;
     if (pl.B2) {
@@ -1120,6 +1433,7 @@ static rv_status set_attrs() {
   RV_CU(cudaFuncSetAttribute(k_combine<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(CombineShared)));
   RV_CU(cudaFuncSetAttribute(k_hist<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, SC_WARPS * 2048 * 4));
   RV_CU(cudaFuncSetAttribute(k_scatter<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, SC_WARPS * 2048 * 4));
+  RV_CU(cudaFuncSetAttribute(k_scatter_tile<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TileShared<F>)));
   g_attr_done[F] = true;
   return RV_OK;
 }
