@@ -169,6 +169,24 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def combine_ranks(ms, verified, n_local, world):
+    """Whole-job numbers from per-rank ones: the step time is the slowest
+    rank's, the run is verified only if every rank's is, and the value counts
+    the events of all ranks (weak scaling: each rank has its own trace)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([ms, 0.0 if verified else 1.0], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        n = torch.tensor([float(n_local)], dtype=torch.float64, device=dev)
+        dist.all_reduce(n, op=dist.ReduceOp.SUM)
+        ms, verified, n_total = float(t[0]), bool(t[1].item() == 0.0), float(n[0])
+    else:
+        n_total = float(n_local)
+    return ms, verified, n_total / (ms / 1e3)
+
+
 def workload_name(k):
     w = WORKLOADS[k]
     if w["kind"] == "socket":
@@ -247,14 +265,7 @@ def main():
     ms = e0.elapsed_time(e1) / args.steps
     last = rv.parse_result(bytes(dres.cpu().numpy()))
     verified &= last.root == first.root and last.root_counts == first.root_counts
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        v = torch.tensor([1 if verified else 0], device="cuda")
-        dist.all_reduce(v, op=dist.ReduceOp.MIN)
-        verified = bool(v.item())
-    value = n * world / (ms / 1e3)
+    ms, verified, value = combine_ranks(ms, verified, n, world)
 
     # per-kernel durations (CUDA events on the launch stream) over a second timed pass
     rv.lib().rv_profile_enable(1)
