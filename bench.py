@@ -204,7 +204,16 @@ def main():
     ap.add_argument("--workload", default="c2", choices=list(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--events", type=int, default=0,
+                    help="shrink the workload to about this many events (ids scale with it); profiling only")
     args = ap.parse_args()
+    if args.events:
+        w = WORKLOADS[args.workload]
+        scale = args.events / w["n"]
+        w["n"] = args.events
+        for k in ("n_ids", "n_users"):
+            if k in w:
+                w[k] = max(10, int(w[k] * scale))
     if args.impl == "reference":
         return run_reference(args)
     if WORKLOADS[args.workload]["kind"] == "batch":
