@@ -29,6 +29,7 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "profile.h"
@@ -46,11 +47,9 @@ constexpr int HT_BITS = 11;
 constexpr int HT_CAP = 1 << HT_BITS;
 constexpr int UCAP = 256;
 constexpr int GC = 16;
-constexpr int TILE2 = 8192;
 constexpr int COLCHUNK = 64;
 constexpr uint16_t NO_SLOT = 0xFFFF;
 constexpr uint16_t FULL_SLOT = 0xFFFE;
-constexpr uint16_t DOM_SLOT = 0xFFFD;   // record of the unit's dominant-candidate key
 constexpr uint64_t EMPTY_KEY = ~0ull;
 constexpr unsigned FULL = 0xFFFFFFFFu;
 constexpr int SPIN_LIMIT = 1 << 22;
@@ -146,6 +145,9 @@ template <int F> struct TileSize { static constexpr int v = 4096; };
 template <> struct TileSize<FMT_K32> { static constexpr int v = 8192; };
 constexpr int TB_THREADS = 256;
 constexpr int TB_WARPS = TB_THREADS / 32;
+// records of one level-2 tile (a piece of a first-level bucket)
+template <int F> struct Tile2Len { static constexpr int v = 4096; };
+template <> struct Tile2Len<FMT_K32> { static constexpr int v = 8192; };
 
 template <int F>
 __global__ void __launch_bounds__(TB_THREADS)
@@ -270,6 +272,45 @@ k_scatter_tile(const void* keyp, const uint8_t* pred, uint64_t n, int nq, int n_
     out[S.gbase[b] + (i - S.loc[b])] = S.orec[i];
   }
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&acc->err, ERR_LETTER);
+}
+
+// Rank of each lane's bucket b among the records of its warp so far: lanes of
+// equal buckets are matched by ballots and the lowest of them advances the
+// warp's counter (equal buckets never share a leader, so no atomics).
+template <int BITS>
+__device__ __forceinline__ uint32_t warp_rank(uint32_t b, bool v, uint32_t* cnt, uint32_t lt) {
+  const uint32_t peers = match_bits<BITS>(b, v);
+  const int ld = __ffs(peers) - 1;
+  uint32_t old = 0;
+  if (v && (int)(threadIdx.x & 31) == ld) {
+    old = cnt[b];
+    cnt[b] = old + __popc(peers);
+  }
+  old = __shfl_sync(FULL, old, ld);
+  return old + __popc(peers & lt);
+}
+
+// Exclusive scan of a tile's per-warp bucket counts (thread b owns bucket b):
+// loc[b] = start of bucket b in the tile, wcur[w][b] = cursor of warp w.
+template <int NB>
+__device__ __forceinline__ void tile_scan(uint32_t (*wcur)[NB], uint32_t* loc, uint32_t* tsum, int nb) {
+  const int b = threadIdx.x, lane = b & 31, wl = b >> 5;
+  uint32_t tot = 0;
+  if (b < nb)
+    for (int w = 0; w < TB_WARPS; ++w) tot += wcur[w][b];
+  uint32_t x = tot;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(FULL, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) tsum[wl] = x;
+  __syncthreads();
+  uint32_t run = x - tot;
+  for (int w = 0; w < wl; ++w) run += tsum[w];
+  if (b < nb) {
+    loc[b] = run;
+    for (int w = 0; w < TB_WARPS; ++w) { const uint32_t c = wcur[w][b]; wcur[w][b] = run; run += c; }
+  }
 }
 
 // per (bucket, chunk of warps): chunk sums
@@ -444,9 +485,43 @@ __global__ void __launch_bounds__(1024) k_scan_u32(const uint32_t* cnt, int P, u
   if (t == 0) *n = carry;
 }
 
-// one thread per tile: binary search of its bucket in first[]
+// Units of the fold.  A bucket longer than half a unit is cut into
+// ceil(len / unit) units; with `pack`, the shorter buckets of one first-level
+// bucket whose starts fall into the same half-unit window share one unit,
+// which is then at most one unit long and holds whole buckets only.  K[b] is
+// the number of units starting at bucket b and uend[b] the end of a shared
+// unit.
+__global__ void k_count_units(const uint64_t* bstart, int P, int B2, uint64_t unit, int pack, uint32_t* K,
+                              uint64_t* uend) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= P) return;
+  const uint64_t s = bstart[b], len = bstart[b + 1] - s, W = unit / 2;
+  if (!pack || len > W) {
+    K[b] = (uint32_t)((len + unit - 1) / unit);
+    return;
+  }
+  const int first = (b >> B2) << B2, last = first + (1 << B2);
+  const uint64_t base = bstart[first], g = (s - base) / W;
+  const bool head = b == first || bstart[b] - bstart[b - 1] > W || (bstart[b - 1] - base) / W != g;
+  if (!head) {
+    K[b] = 0;
+    return;
+  }
+  int e = b;
+  while (e + 1 < last) {
+    const uint64_t s1 = bstart[e + 1];
+    if (bstart[e + 2] - s1 > W || (s1 - base) / W != g) break;
+    ++e;
+  }
+  const uint64_t end = bstart[e + 1];
+  K[b] = end > s ? 1u : 0u;
+  uend[b] = end;
+}
+
+// one thread per tile: binary search of its bucket in first[]; with uend, a
+// bucket of at most half a tile heads a shared tile that ends at uend[b]
 __global__ void k_emit_tiles(const uint64_t* bstart, int P, uint64_t tile_len, const uint32_t* first, const uint32_t* K,
-                             const unsigned int* n_tiles, Tile* tiles) {
+                             const unsigned int* n_tiles, Tile* tiles, const uint64_t* uend = nullptr) {
   const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= *n_tiles) return;
   int lo = 0, hi = P - 1;            // last bucket with first[b] <= t and K[b] > 0
@@ -460,6 +535,7 @@ __global__ void k_emit_tiles(const uint64_t* bstart, int P, uint64_t tile_len, c
   tl.bucket = (uint32_t)lo; tl.k = j; tl.K = K[lo]; tl.pad = 0;
   tl.begin = bstart[lo] + j * tile_len;
   tl.end = min(bstart[lo + 1], tl.begin + tile_len);
+  if (uend && bstart[lo + 1] - bstart[lo] <= tile_len / 2) tl.end = uend[lo];
   tiles[t] = tl;
 }
 
@@ -515,6 +591,8 @@ __global__ void k_scan2(uint32_t* hist2, const uint32_t* tfirst, const uint32_t*
   tot2[t] = run;
 }
 
+// Level-2 split of 32-bit records, one warp per tile: each warp keeps
+// private sub-bucket cursors and writes every record directly.
 template <int F>
 __global__ void __launch_bounds__(SC_WARPS * 32)
 k_scatter2(const typename RecT<F>::type* in, const Tile* tiles, const unsigned int* n_tiles, int B1, int B2,
@@ -552,6 +630,77 @@ k_scatter2(const typename RecT<F>::type* in, const Tile* tiles, const unsigned i
       __syncwarp();
       if (v) out[pos] = rec[j];
     }
+  }
+}
+
+// Level-2 split of 64-bit records, one CTA per tile of a first-level bucket:
+// records stay in registers with their rank, are grouped by sub-bucket in
+// shared memory, and every sub-bucket's run is written out contiguously
+// (8-byte records scattered one by one from a warp waste most of each
+// written sector).
+template <int F>
+struct Tile2Shared {
+  typename RecT<F>::type orec[Tile2Len<F>::v];
+  uint32_t ibr[Tile2Len<F>::v];
+  uint8_t ob[Tile2Len<F>::v];
+  uint32_t wcur[TB_WARPS][128];
+  uint32_t loc[128];
+  uint64_t gbase[128];
+  uint32_t tsum[TB_WARPS];
+};
+
+template <int F>
+__global__ void __launch_bounds__(TB_THREADS, 2)
+k_scatter2_tile(const typename RecT<F>::type* in, const Tile* tiles, const unsigned int* n_tiles, int B1, int B2,
+                const uint32_t* pre2, const uint64_t* bstart2, typename RecT<F>::type* out) {
+  typedef typename RecT<F>::type Rec;
+  constexpr int T = Tile2Len<F>::v, R = T / TB_THREADS, PER = T / TB_WARPS;
+  extern __shared__ __align__(16) unsigned char tile2_smem[];
+  Tile2Shared<F>& S = *reinterpret_cast<Tile2Shared<F>*>(tile2_smem);
+  const uint32_t tile = blockIdx.x;
+  if (tile >= *n_tiles) return;
+  const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t lt = lanemask_lt();
+  const int P2 = 1 << B2;
+  const Tile tl = tiles[tile];
+  const int len = (int)(tl.end - tl.begin);      // <= T by construction
+  for (int i = threadIdx.x; i < TB_WARPS * 128; i += TB_THREADS) S.wcur[i / 128][i % 128] = 0;
+  __syncthreads();
+  const int sh = sub_shift<F>(B1, B2);
+  const int w0 = wl * PER;
+  const Rec* ip = in + tl.begin;
+  Rec rec[R];
+#pragma unroll
+  for (int j = 0; j < R; ++j) {
+    const int i = w0 + j * 32 + lane;
+    rec[j] = i < len ? ip[i] : (Rec)0;
+  }
+#pragma unroll
+  for (int j = 0; j < R; ++j) {
+    const int i = w0 + j * 32 + lane;
+    const bool v = i < len;
+    const uint32_t b = (uint32_t)((uint64_t)rec[j] >> sh) & (uint32_t)(P2 - 1);
+    const uint32_t rank = warp_rank<7>(b, v, S.wcur[wl], lt);
+    if (v) S.ibr[i] = b | (rank << 8);
+  }
+  __syncthreads();
+  tile_scan<128>(S.wcur, S.loc, S.tsum, P2);
+  if ((int)threadIdx.x < P2)
+    S.gbase[threadIdx.x] = bstart2[((uint64_t)tl.bucket << B2) + threadIdx.x] + pre2[(uint64_t)tile * P2 + threadIdx.x];
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < R; ++j) {
+    const int i = w0 + j * 32 + lane;
+    if (i < len) {
+      const uint32_t br = S.ibr[i], b = br & 0xFFu, pos = S.wcur[wl][b] + (br >> 8);
+      S.orec[pos] = rec[j];
+      S.ob[pos] = (uint8_t)b;
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < len; i += TB_THREADS) {
+    const uint32_t b = S.ob[i];
+    out[S.gbase[b] + (i - S.loc[b])] = S.orec[i];
   }
 }
 
@@ -684,59 +833,75 @@ __device__ __forceinline__ void root_delta(const Params& p, uint32_t stream, uin
   atomicAdd(&p.ss.root[stream * 6 + to], 1ull);
 }
 
+// Streaming: the binding continues from its stored state; a verdict change
+// becomes count deltas (out of line: the plain offline fold never takes it).
+template <int F>
+__device__ __noinline__ void finalize_stream(const Params& p, OuterTable* U, uint64_t skey, uint64_t M, uint32_t b1) {
+  const uint32_t b = p.nq == 2 ? (uint32_t)(skey & 0xFFFFFFFFull) : (uint32_t)original_key<F>(skey, b1, p.B1, p.nq);
+  const uint32_t old = p.ss.bstate[b];
+  const bool seen = old & 0x80u;
+  const uint32_t st = seen ? (old & 15u) : (uint32_t)p.tab.q0;
+  const uint32_t ns = (uint32_t)((M >> (4 * st)) & 15ull);
+  const uint32_t v = p.tab.labels[ns];
+  const uint32_t vold = seen ? p.ss.bverdict[b] : 0xFFu;
+  p.ss.bstate[b] = (uint8_t)(0x80u | ns);
+  p.ss.bverdict[b] = (uint8_t)v;
+  if constexpr (F != FMT_K2) {
+    root_delta(p, p.ss.bstream[b], vold, v);
+  } else {
+    const int ui = outer_slot(*U, (uint32_t)(skey >> 32));
+    if (ui < 0) atomicOr(&p.acc->err, ERR_OUTER_FULL);
+    else if (vold != v) {
+      atomicAdd(&U->ucnt[ui][v], 1u);
+      if (vold != 0xFFu) atomicAdd(&U->ucnt[ui][vold], 0xFFFFFFFFu);   // -1
+    }
+  }
+}
+
+// count verdict v under the binding's outer value (two quantifiers)
+__device__ __noinline__ void count_outer(const Params& p, OuterTable* U, uint64_t skey, uint32_t v) {
+  const int ui = outer_slot(*U, (uint32_t)(skey >> 32));
+  if (ui < 0) atomicOr(&p.acc->err, ERR_OUTER_FULL);
+  else atomicAdd(&U->ucnt[ui][v], 1u);
+}
+
+// per-binding output record
+template <int F>
+__device__ __noinline__ void emit_binding(const Params& p, uint64_t skey, uint32_t b1, uint32_t v) {
+  unsigned long long idx = atomicAdd(&p.acc->n_out, 1ull);
+  if (idx < p.out.capacity) {
+    p.out.keys[idx] = original_key<F>(skey, b1, p.B1, p.nq);
+    p.out.verdicts[idx] = (uint8_t)v;
+  }
+}
+
 // verdict of one innermost binding whose composed map over its whole cluster is M
 template <int F>
-__device__ __forceinline__ void finalize_slot(const Params& p, FinalCtx& fc, OuterTable& U, uint64_t skey,
+__device__ __forceinline__ void finalize_slot(const Params& p, FinalCtx& fc, OuterTable* U, uint64_t skey,
                                               uint64_t M, uint32_t bucket) {
   const uint32_t b1 = bucket >> p.B2;
   if (p.stream_mode) {
-    // continue from the binding's stored state; turn a verdict change into deltas
-    const uint32_t b = p.nq == 2 ? (uint32_t)(skey & 0xFFFFFFFFull) : (uint32_t)original_key<F>(skey, b1, p.B1, p.nq);
-    const uint32_t old = p.ss.bstate[b];
-    const bool seen = old & 0x80u;
-    const uint32_t st = seen ? (old & 15u) : (uint32_t)p.tab.q0;
-    const uint32_t ns = (uint32_t)((M >> (4 * st)) & 15ull);
-    const uint32_t v = p.tab.labels[ns];
-    const uint32_t vold = seen ? p.ss.bverdict[b] : 0xFFu;
-    p.ss.bstate[b] = (uint8_t)(0x80u | ns);
-    p.ss.bverdict[b] = (uint8_t)v;
-    if (p.nq <= 1) {
-      root_delta(p, p.ss.bstream[b], vold, v);
-    } else {
-      const int ui = outer_slot(U, (uint32_t)(skey >> 32));
-      if (ui < 0) atomicOr(&p.acc->err, ERR_OUTER_FULL);
-      else if (vold != v) {
-        atomicAdd(&U.ucnt[ui][v], 1u);
-        if (vold != 0xFFu) atomicAdd(&U.ucnt[ui][vold], 0xFFFFFFFFu);   // -1
-      }
-    }
+    finalize_stream<F>(p, U, skey, M, b1);
     return;
   }
-  const uint32_t state = (uint32_t)((M >> (4 * p.tab.q0)) & 15ull);
-  const uint32_t v = p.tab.labels[state];
-  if (p.nq <= 1) {
+  const uint32_t v = p.tab.labels[(uint32_t)((M >> (4 * p.tab.q0)) & 15ull)];
+  if constexpr (F != FMT_K2) {
     inc6(fc.h0, v);
     fc.nodes0 += 1;
   } else {
     inc6(fc.h1, v);
     fc.nodes1 += 1;
-    int ui = outer_slot(U, (uint32_t)(skey >> 32));
-    if (ui < 0) atomicOr(&p.acc->err, ERR_OUTER_FULL);
-    else atomicAdd(&U.ucnt[ui][v], 1u);
+    count_outer(p, U, skey, v);
   }
-  if (p.out.keys) {
-    unsigned long long idx = atomicAdd(&p.acc->n_out, 1ull);
-    if (idx < p.out.capacity) {
-      p.out.keys[idx] = original_key<F>(skey, b1, p.B1, p.nq);
-      p.out.verdicts[idx] = (uint8_t)v;
-    }
-  }
+  if (p.out.keys) emit_binding<F>(p, skey, b1, v);
 }
 
 // after all innermost bindings of a bucket: valuate its outer nodes (level 1)
 template <int F>
-__device__ void finalize_outer(const Params& p, FinalCtx& fc, OuterTable& U, uint32_t bucket) {
-  if (p.nq != 2) return;
+__device__ void finalize_outer(const Params& p, FinalCtx& fc, OuterTable* Up, uint32_t bucket) {
+  if constexpr (F != FMT_K2) return;
+  else {
+  OuterTable& U = *Up;
   const unsigned int nu = min(U.nu, (unsigned int)UCAP);
   const uint32_t b1 = bucket >> p.B2;
   for (unsigned int i = threadIdx.x; i < nu; i += blockDim.x) {
@@ -767,6 +932,7 @@ __device__ void finalize_outer(const Params& p, FinalCtx& fc, OuterTable& U, uin
       }
     }
   }
+  }
 }
 
 __device__ void flush_final(const Params& p, FinalCtx& fc) {
@@ -791,108 +957,366 @@ __device__ __forceinline__ void clear_final(FinalCtx& fc) {
 }
 
 // ------------------------------------------------------------------ fold
-constexpr int UNIT_MAX = 8192;     // records of one unit held in shared memory
+// Capacities of one fold CTA.  Records of one 32-bit key are small, so a unit
+// holds more of them; a 64-bit or two-variable key brings larger binding
+// tables (a nested trace has a few hundred innermost bindings per bucket).
+template <int F> struct FoldCfg {
+  static constexpr int UNIT = 8192, SL = 1024, HTB = 11, RB = 8, MINB = 2;
+};
+template <> struct FoldCfg<FMT_K32> {   // records come from shared memory: no load batching
+  static constexpr int UNIT = 8192, SL = 512, HTB = 10, RB = 1, MINB = 3;
+};
 
+// A record's fold word: letter | slot << 8 | rank << 18, or letter | PK_OUT
+// for a record outside the current pass.  The rank of a record is its index
+// among the records of its slot in its warp's slice, so 10 bits suffice for
+// slices of at most 1024 records.
+constexpr uint32_t PK_OUT = 1u << 28;
+constexpr uint16_t NO_POS = 0xFFFF;
+static_assert(FoldCfg<FMT_K32>::UNIT / FOLD_WARPS <= 1024 && FoldCfg<FMT_K64>::UNIT / FOLD_WARPS <= 1024,
+              "ranks are 10 bits");
+static_assert(FoldCfg<FMT_K64>::SL <= 1024 && FoldCfg<FMT_K32>::SL <= 1024, "slots are 10 bits");
+
+struct NoOuter {};
+
+template <int F>
 struct FoldShared {
+  static constexpr int UNIT = FoldCfg<F>::UNIT, SL = FoldCfg<F>::SL, HT = 1 << FoldCfg<F>::HTB;
+  static constexpr bool PACKED = F == FMT_K32;     // table entry = key << 32 | slot
   uint64_t lmap[RV_MAX_LETTERS];
-  SlotTable T;
-  OuterTable U;
-  uint8_t letter[UNIT_MAX];
-  uint16_t slot_of[UNIT_MAX];          // NO_SLOT: record outside the current pass
-  uint8_t sorted[UNIT_MAX];            // letters grouped by slot, trace order kept
-  uint32_t wcnt[FOLD_WARPS][SLOTS / 2];  // two 16-bit per-warp counters (then cursors) per word
-  uint32_t seg[SLOTS + 1];
-  uint32_t tsum[FOLD_WARPS];
+  // fold word of every record of the unit; 32-bit records arrive here by one
+  // bulk copy (16-byte aligned, so up to 4 extra records at either end)
+  uint32_t pk[UNIT + 8];
+  uint8_t sorted[UNIT];                // letters grouped by slot, trace order kept
+  uint64_t tkey[HT];
+  uint16_t tslot[PACKED ? 2 : HT];     // slot of tkey[h] (64-bit keys)
+  uint64_t skey[SL];                   // key of every slot
+  uint16_t hpos[SL];                   // table position of every slot (NO_POS: none)
+  uint16_t wc[FOLD_WARPS][SL];         // per-warp counts of every slot, then cursors
+  uint32_t seg[SL + 1];                // run of every slot in `sorted`
   uint64_t firstmap[FOLD_THREADS];     // map of a piece's first run when that run began earlier
   uint64_t lastval[FOLD_THREADS];      // state or map of a piece's last run when it goes on
   uint64_t wmaps[FOLD_WARPS];
-  int dom;                             // 1 when slot 0 is the dominant candidate in this pass
-  uint32_t pass_bits[64], pass_val[64];
+  uint32_t tsum[FOLD_WARPS];
+  typename std::conditional<F == FMT_K2, OuterTable, NoOuter>::type U;
+  Tile tile, ntile;                    // current and next unit
+  unsigned int cur, ncur;
+  uint64_t mbar;                       // completion of the bulk copy
+  unsigned int bad;
+  unsigned int nslots, ovf;
   int npass;
+  uint32_t pass_bits[64], pass_val[64];
   uint64_t item_off;
   uint32_t item_cnt;
 };
 
-__device__ __forceinline__ uint32_t wc_get(const uint32_t* row, uint32_t s) { return (row[s >> 1] >> (16 * (s & 1))) & 0xFFFFu; }
+// MINB CTAs per SM must fit the SM's 228 KB of shared memory (1 KB of it reserved per CTA)
+static_assert(FoldCfg<FMT_K32>::MINB * (sizeof(FoldShared<FMT_K32>) + 1024) <= 228 * 1024, "fold CTAs per SM");
+static_assert(FoldCfg<FMT_K64>::MINB * (sizeof(FoldShared<FMT_K64>) + 1024) <= 228 * 1024, "fold CTAs per SM");
+static_assert(FoldCfg<FMT_K2>::MINB * (sizeof(FoldShared<FMT_K2>) + 1024) <= 228 * 1024, "fold CTAs per SM");
 
-// Fold of one unit: (1) slot of every record, (2) stable counting sort of the
-// unit's letters by slot (per-warp counts over contiguous slices), (3) each
-// binding's run of letters is folded -- short runs by one thread, long runs by
-// a warp composing per-lane maps and combining them in lane order.
 template <int F>
-__global__ void __launch_bounds__(FOLD_THREADS, 2)
+__device__ __forceinline__ OuterTable* outer_of(FoldShared<F>& S) {
+  if constexpr (F == FMT_K2) return &S.U;
+  else return nullptr;
+}
+
+template <int F>
+__device__ __forceinline__ uint32_t fold_home(uint64_t key) {
+  // the low bits of a mixed key are uniform; a two-variable key carries the
+  // raw inner value there, so it is hashed again
+  if constexpr (F == FMT_K2) return (uint32_t)(key_mult(key) >> (64 - FoldCfg<F>::HTB));
+  else return (uint32_t)key & ((1u << FoldCfg<F>::HTB) - 1);
+}
+
+constexpr int PROBE_NEED = -2;   // key absent: the probe ended at an empty entry
+// low word of a 32-bit-key entry while its slot is being taken, and when the
+// slot table was full
+constexpr uint32_t E_PENDING = 0xFFFFFFFFu, E_FULL = 0xFFFFFFFEu;
+
+// Slot stored with (or beside) the table entry at h whose key matched; waits,
+// boundedly, while the inserting lane publishes it.  -1: no slot.
+template <int F>
+__device__ __forceinline__ int fold_entry_slot(FoldShared<F>& S, uint32_t h, uint64_t e, Acc* acc) {
+  int spins = 0;
+  if constexpr (FoldShared<F>::PACKED) {
+    volatile uint64_t* vk = S.tkey;
+    while ((uint32_t)e == E_PENDING) {
+      if (++spins > SPIN_LIMIT) { atomicOr(&acc->err, ERR_SPIN); return -1; }
+      e = vk[h];
+    }
+    return (uint32_t)e == E_FULL ? -1 : (int)(uint32_t)e;
+  } else {
+    volatile uint16_t* vs = S.tslot;
+    uint16_t sl;
+    while ((sl = vs[h]) == NO_SLOT) {
+      if (++spins > SPIN_LIMIT) { atomicOr(&acc->err, ERR_SPIN); return -1; }
+    }
+    return sl == FULL_SLOT ? -1 : (int)sl;
+  }
+}
+
+template <int F>
+__device__ __forceinline__ bool fold_key_is(uint64_t e, uint64_t key) {
+  if constexpr (FoldShared<F>::PACKED) return (e >> 32) == key;
+  else return e == key;
+}
+
+// Lookup without insertion: the slot of key, PROBE_NEED, or -1 (table full or
+// a bounded wait gave up).
+template <int F>
+__device__ __forceinline__ int fold_probe(FoldShared<F>& S, uint64_t key, Acc* acc) {
+  constexpr int HT = FoldShared<F>::HT;
+  uint32_t h = fold_home<F>(key);
+  volatile uint64_t* vk = S.tkey;
+  for (int probe = 0; probe < HT; ++probe) {
+    const uint64_t e = vk[h];
+    if (e == EMPTY_KEY) return PROBE_NEED;
+    if (fold_key_is<F>(e, key)) return fold_entry_slot<F>(S, h, e, acc);
+    h = (h + 1) & (HT - 1);
+  }
+  S.ovf = 1;
+  return -1;
+}
+
+// Insertion by one lane: the entry is claimed first, then a slot number is
+// taken and published; lanes that meet the claimed entry wait for it.
+// Returns -1 when the slot table is full (the pass then restarts split).
+template <int F>
+__device__ __noinline__ int fold_insert(FoldShared<F>& S, uint64_t key, Acc* acc) {
+  constexpr int HT = FoldShared<F>::HT, SL = FoldShared<F>::SL;
+  constexpr bool PK = FoldShared<F>::PACKED;
+  uint32_t h = fold_home<F>(key);
+  volatile uint64_t* vk = S.tkey;
+  for (int probe = 0; probe < HT; ++probe) {
+    uint64_t e = vk[h];
+    if (e == EMPTY_KEY) {
+      const uint64_t claim = PK ? (key << 32) | E_PENDING : key;
+      const unsigned long long prev = atomicCAS((unsigned long long*)&S.tkey[h], (unsigned long long)EMPTY_KEY,
+                                                (unsigned long long)claim);
+      if (prev == EMPTY_KEY) {
+        const unsigned int s = atomicAdd(&S.nslots, 1u);
+        const bool full = s >= (unsigned int)SL;
+        if (full) S.ovf = 1;
+        else { S.skey[s] = key; S.hpos[s] = (uint16_t)h; }
+        __threadfence_block();
+        if constexpr (PK) vk[h] = (key << 32) | (full ? E_FULL : s);
+        else *(volatile uint16_t*)&S.tslot[h] = full ? FULL_SLOT : (uint16_t)s;
+        return full ? -1 : (int)s;
+      }
+      e = prev;
+    }
+    if (fold_key_is<F>(e, key)) return fold_entry_slot<F>(S, h, e, acc);
+    h = (h + 1) & (HT - 1);
+  }
+  S.ovf = 1;
+  return -1;
+}
+
+// Slot of every lane's key: one probe per lane, then the keys still absent are
+// inserted one distinct key at a time (lanes holding the same new key share
+// the insertion).
+template <int F>
+__device__ __forceinline__ int warp_slot(FoldShared<F>& S, uint64_t key, bool want, Acc* acc) {
+  int slot = want ? fold_probe<F>(S, key, acc) : -1;
+  uint32_t need = __ballot_sync(FULL, slot == PROBE_NEED);
+  while (need) {
+    const int ld = __ffs(need) - 1;
+    const uint64_t k = __shfl_sync(FULL, key, ld);
+    int s = 0;
+    if ((int)(threadIdx.x & 31) == ld) s = fold_insert<F>(S, key, acc);
+    s = __shfl_sync(FULL, s, ld);
+    if (slot == PROBE_NEED && key == k) slot = s;
+    need = __ballot_sync(FULL, slot == PROBE_NEED);
+  }
+  return slot;
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// One-shot bulk copy global -> shared that completes on an mbarrier (the
+// barrier expects `bytes`; both addresses and the size are multiples of 16).
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+
+// Wait for phase `parity` of the mbarrier, for at most about a second.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_addr(bar);
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(ok)
+                 : "r"(a), "r"(parity)
+                 : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > (1ll << 31)) return false;
+  }
+}
+
+// Fold of one unit (a contiguous range of one bucket's records):
+// (1) every warp takes a contiguous slice and gives each record its slot and
+//     its rank among the slot's records of the slice (ballot match per round);
+// (2) one scan over (slot, warp) turns the per-warp counts into cursors;
+// (3) each letter goes to cursor + rank, so the unit's letters are grouped by
+//     binding with trace order kept;
+// (4) each binding's run is folded: every thread an equal piece, runs that
+//     cross pieces joined in order (plain state steps when the run starts at
+//     the bucket's start, map composition otherwise).
+// The key of the unit's first record is a candidate for a dominant binding
+// (a Zipf head): when it holds at least half of the unit its records stay in
+// place and are folded as contiguous pieces instead of being sorted.
+template <int F>
+__global__ void __launch_bounds__(FOLD_THREADS, FoldCfg<F>::MINB)
 k_fold(const typename RecT<F>::type* recs, const Tile* units, const unsigned int* n_units, Params p,
        Item* items, Pair* pool) {
+  typedef typename RecT<F>::type Rec;
+  constexpr int SL = FoldCfg<F>::SL, HT = 1 << FoldCfg<F>::HTB, RB = FoldCfg<F>::RB;
   extern __shared__ __align__(16) unsigned char fold_smem[];
-  FoldShared& S = *reinterpret_cast<FoldShared*>(fold_smem);
+  FoldShared<F>& S = *reinterpret_cast<FoldShared<F>*>(fold_smem);
   const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31, nthr = FOLD_THREADS;
   const int ns = p.tab.n_states;
   const uint32_t lt = lanemask_lt();
   for (int i = threadIdx.x; i < RV_MAX_LETTERS; i += nthr) S.lmap[i] = p.tab.maps[i];
+  for (int i = threadIdx.x; i < HT; i += nthr) {
+    S.tkey[i] = EMPTY_KEY;
+    if constexpr (!FoldShared<F>::PACKED) S.tslot[i] = NO_SLOT;
+  }
+  for (int i = threadIdx.x; i < FOLD_WARPS * SL; i += nthr) S.wc[i / SL][i % SL] = 0;
   FinalCtx fc;
   clear_final(fc);
-  __shared__ unsigned int s_next;
   const unsigned int nun = *n_units;
+  constexpr bool BULK = F == FMT_K32;   // records reach shared memory by a bulk copy
+  uint32_t bulk_phase = 0;
+  if (threadIdx.x == 0) {
+    S.cur = atomicAdd(&p.acc->next_unit, 1u);
+    if (S.cur < nun) S.tile = units[S.cur];
+    S.bad = 0;
+    if constexpr (BULK) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&S.mbar)) : "memory");
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+  }
   while (true) {
     __syncthreads();
-    if (threadIdx.x == 0) s_next = atomicAdd(&p.acc->next_unit, 1u);
-    __syncthreads();
-    const unsigned int u = s_next;
-    if (u >= nun) break;
-    const Tile t = units[u];
+    const unsigned int u = S.cur;
+    if (u >= nun || S.bad) break;
+    const Tile t = S.tile;
+    unsigned int nxt = 0;
+    Tile tn{};
+    if (threadIdx.x == 0) nxt = atomicAdd(&p.acc->next_unit, 1u);   // claimed now, used at the end
+    bool ahead = false;                                             // next unit looked up yet
     const bool single = t.K == 1;
     const bool use_state = single && !p.stream_mode;   // a single unit starting at q0: plain states
-    const int len = (int)(t.end - t.begin);            // <= UNIT_MAX by construction
+    const int len = (int)(t.end - t.begin);            // <= FoldCfg<F>::UNIT by construction
     if (threadIdx.x == 0) {
       S.npass = 1; S.pass_bits[0] = 0; S.pass_val[0] = 0;
       S.item_cnt = 0;
       S.item_off = single ? 0 : atomicAdd(&p.acc->pair_top[0], (unsigned long long)len);
     }
-    if (t.k == 0) reset_outer(S.U);
+    if constexpr (F == FMT_K2) {
+      if (t.k == 0) reset_outer(S.U);
+    }
     const int per = (len + FOLD_WARPS - 1) / FOLD_WARPS;
     const int w0 = min(len, wl * per), w1 = min(len, w0 + per);
+    // 32-bit records: the unit's records, copied in whole 16-byte words
+    const char* ra = (const char*)(recs + t.begin);
+    const char* ra16 = (const char*)((uintptr_t)ra & ~(uintptr_t)15);
+    const uint32_t rbytes = (uint32_t)((((uintptr_t)(recs + t.end) + 15) & ~(uintptr_t)15) - (uintptr_t)ra16);
+    uint32_t* P = S.pk + (BULK ? (ra - ra16) / 4 : 0);   // fold word of record i: P[i]
+    uint64_t cand = BULK ? 0 : (uint64_t)recs[t.begin] >> 8;
     while (true) {
       __syncthreads();
       if (S.npass == 0) break;
       const int bits = (int)S.pass_bits[S.npass - 1];
       const uint32_t val = S.pass_val[S.npass - 1];
-      // The key of the unit's first record is the dominant candidate: under a
-      // Zipf law one key fills most records of a heavy unit.  It takes slot 0
-      // and its records skip hashing and sorting (folded in place below).
-      const uint64_t cand = (uint64_t)recs[t.begin] >> 8;
-      const bool dom = in_pass(cand, bits, val);
-      reset_table(S.T);
+      if constexpr (BULK) {
+        // every pass reads the records afresh: the previous one overwrote them
+        if (threadIdx.x == 0) {
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          bulk_load(S.pk, ra16, rbytes, &S.mbar);
+        }
+        if (!mbar_wait(&S.mbar, bulk_phase)) atomicOr(&S.bad, 1u);
+        bulk_phase ^= 1u;
+        cand = P[0] >> 8;
+      }
+      const bool cand_in = in_pass(cand, bits, val);
+      if (threadIdx.x == 0) {
+        // slot 0 belongs to the candidate; its records never touch the table
+        S.nslots = cand_in ? 1u : 0u;
+        S.ovf = 0;
+        if (cand_in) { S.skey[0] = cand; S.hpos[0] = NO_POS; }
+      }
       __syncthreads();
-      if (threadIdx.x == 0 && dom) find_or_insert(S.T, cand, p.acc, [](unsigned int) {});
-      __syncthreads();
-      // 1. letters and binding slots; RB records per thread are loaded together
-      constexpr int RB = 16;
-      for (int i0 = threadIdx.x; i0 < len; i0 += nthr * RB) {
-        uint64_t r[RB];
+      if (S.bad) {
+        // the copy never completed: report, give it another bounded wait, stop
+        if (threadIdx.x == 0) {
+          atomicOr(&p.acc->err, ERR_SPIN);
+          mbar_wait(&S.mbar, bulk_phase ^ 1u);
+        }
+        break;
+      }
+      // 1. slot and rank of every record of this warp's slice
+#pragma unroll 1
+      for (int base = w0; base < w1; base += 32 * RB) {
+        Rec r[RB];
 #pragma unroll
         for (int j = 0; j < RB; ++j) {
-          const int i = i0 + j * nthr;
-          r[j] = i < len ? (uint64_t)recs[t.begin + i] : 0ull;
+          const int i = base + j * 32 + lane;
+          r[j] = i < w1 ? (BULK ? (Rec)P[i] : recs[t.begin + i]) : (Rec)0;
         }
 #pragma unroll
         for (int j = 0; j < RB; ++j) {
-          const int i = i0 + j * nthr;
-          if (i < len) {
-            const uint64_t key = r[j] >> 8;
-            uint16_t slv = NO_SLOT;
-            if (dom && key == cand) {
-              slv = DOM_SLOT;
-            } else if (in_pass(key, bits, val)) {
-              const int sl = find_or_insert(S.T, key, p.acc, [](unsigned int) {});
-              if (sl >= 0) slv = (uint16_t)sl;
+          if (base + j * 32 >= w1) break;                  // warp-uniform
+          const int i = base + j * 32 + lane;
+          const bool valid = i < w1;
+          const uint64_t key = (uint64_t)r[j] >> 8;
+          const uint32_t letter = (uint32_t)r[j] & 0xFFu;
+          const bool in = valid && in_pass(key, bits, val);
+          const bool is_cand = in && cand_in && key == cand;
+          if (__all_sync(FULL, is_cand || !valid)) {
+            // a round of the candidate only (the common case under a Zipf head)
+            const uint32_t vm = __ballot_sync(FULL, valid);
+            uint32_t old = 0;
+            if (lane == 0) {
+              old = S.wc[wl][0];
+              S.wc[wl][0] = (uint16_t)(old + __popc(vm));
             }
-            S.slot_of[i] = slv;
-            S.letter[i] = (uint8_t)(r[j] & 0xFF);
+            old = __shfl_sync(FULL, old, 0);
+            if (valid) P[i] = letter | ((old + __popc(vm & lt)) << 18);
+            continue;
           }
+          int slot = warp_slot<F>(S, key, in && !is_cand, p.acc);
+          if (is_cand) slot = 0;
+          const bool v = slot >= 0;
+          const uint32_t mx = __reduce_max_sync(FULL, v ? (uint32_t)slot : 0u);
+          const uint32_t peers = match_nbits(v ? (uint32_t)slot : 0u, v, mx ? 32 - __clz(mx) : 0);
+          const int ld = __ffs(peers) - 1;
+          uint32_t old = 0;
+          if (v && lane == ld) {
+            old = S.wc[wl][slot];
+            S.wc[wl][slot] = (uint16_t)(old + __popc(peers));
+          }
+          old = __shfl_sync(FULL, old, ld);
+          if (valid) P[i] = v ? (letter | ((uint32_t)slot << 8) | ((old + __popc(peers & lt)) << 18)) : (letter | PK_OUT);
         }
       }
       __syncthreads();
-      if (S.T.ovf) {
+      if (!ahead && threadIdx.x == 0) tn = units[nxt < nun ? nxt : nun - 1];   // completes during the scan and placement
+      const unsigned int nsl_all = min(S.nslots, (unsigned int)SL);
+      if (S.ovf) {
+        // too many bindings: clear, then fold this unit in two passes split by a key bit
+        for (int i = threadIdx.x; i < HT; i += nthr) {
+          S.tkey[i] = EMPTY_KEY;
+          if constexpr (!FoldShared<F>::PACKED) S.tslot[i] = NO_SLOT;
+        }
+        for (unsigned int s = threadIdx.x; s < nsl_all; s += nthr)
+          for (int w = 0; w < FOLD_WARPS; ++w) S.wc[w][s] = 0;
+        __syncthreads();
         if (threadIdx.x == 0) {
           S.npass -= 1;
           if (bits >= 20 || S.npass + 2 > 64) {
@@ -906,25 +1330,19 @@ k_fold(const typename RecT<F>::type* recs, const Tile* units, const unsigned int
         }
         continue;
       }
-      const int nsl = (int)min(S.T.nslots, (unsigned int)SLOTS);
-      const int nw = (nsl + 1) / 2;                        // counter words in use per warp
-      const int nbits = nsl > 1 ? 32 - __clz(nsl - 1) : 1;
-      for (int i = threadIdx.x; i < FOLD_WARPS * nw; i += nthr) S.wcnt[i / nw][i % nw] = 0;
-      __syncthreads();
-      // 2. per-warp counts, then an exclusive scan over (slot, warp)
-      for (int i = w0 + lane; i < w1; i += 32) {
-        const uint32_t sl = S.slot_of[i];
-        if (sl < (uint32_t)SLOTS) atomicAdd(&S.wcnt[wl][sl >> 1], 1u << (16 * (sl & 1)));
-      }
-      __syncthreads();
+      const int nsl = (int)nsl_all;
+      // 2. dominant candidate?  then the exclusive scan over (slot, warp)
+      uint32_t c0 = 0;
+      if (cand_in)
+        for (int w = 0; w < FOLD_WARPS; ++w) c0 += S.wc[w][0];
+      const bool dom = cand_in && 2 * c0 >= (uint32_t)len;
       {
-        // thread t owns slot pairs 2t+2k*nthr ... (pairs share a counter word)
-        const int np = nw;                     // slot pairs in use
-        const int pairs_per = (np + nthr - 1) / nthr;
-        const int p0 = min(np, threadIdx.x * pairs_per), p1 = min(np, p0 + pairs_per);
+        const int spt = (nsl + nthr - 1) / nthr;
+        const int s0 = min(nsl, (int)threadIdx.x * spt), s1 = min(nsl, s0 + spt);
         uint32_t sum = 0;
-        for (int q = p0; q < p1; ++q)
-          for (int w = 0; w < FOLD_WARPS; ++w) { const uint32_t word = S.wcnt[w][q]; sum += (word & 0xFFFFu) + (word >> 16); }
+        for (int s = s0; s < s1; ++s)
+          if (!(dom && s == 0))
+            for (int w = 0; w < FOLD_WARPS; ++w) sum += S.wc[w][s];
         uint32_t x = sum;
         for (int o = 1; o < 32; o <<= 1) {
           const uint32_t y = __shfl_up_sync(FULL, x, o);
@@ -934,44 +1352,34 @@ k_fold(const typename RecT<F>::type* recs, const Tile* units, const unsigned int
         __syncthreads();
         uint32_t run = x - sum;
         for (int w = 0; w < wl; ++w) run += S.tsum[w];
-        for (int q = p0; q < p1; ++q) {
-          uint32_t t0 = 0, t1 = 0;
-          for (int w = 0; w < FOLD_WARPS; ++w) { const uint32_t word = S.wcnt[w][q]; t0 += word & 0xFFFFu; t1 += word >> 16; }
-          S.seg[2 * q] = run;
-          S.seg[2 * q + 1] = run + t0;
-          uint32_t c0 = run, c1 = run + t0;
+        for (int s = s0; s < s1; ++s) {
+          S.seg[s] = run;
+          const bool skip = dom && s == 0;
           for (int w = 0; w < FOLD_WARPS; ++w) {
-            const uint32_t word = S.wcnt[w][q];
-            S.wcnt[w][q] = (c0 & 0xFFFFu) | ((c1 & 0xFFFFu) << 16);
-            c0 += word & 0xFFFFu;
-            c1 += word >> 16;
+            const uint32_t c = skip ? 0u : S.wc[w][s];
+            S.wc[w][s] = (uint16_t)run;
+            run += c;
           }
-          run += t0 + t1;
         }
-        if (threadIdx.x == nthr - 1) S.seg[nsl] = run;   // total placed in this pass
+        if (threadIdx.x == nthr - 1) S.seg[nsl] = run;   // records placed in this pass
       }
       __syncthreads();
-      // stable placement: each warp walks its slice in order
-      for (int base = w0; base < w1; base += 32) {
-        const int i = base + lane;
-        const uint32_t sl = i < w1 ? S.slot_of[i] : (uint32_t)NO_SLOT;
-        const bool v = sl < (uint32_t)SLOTS;
-        const uint32_t peers = match_nbits(v ? sl : 0u, v, nbits);
-        uint32_t pos = 0;
-        if (v) pos = wc_get(S.wcnt[wl], sl) + __popc(peers & lt);
-        __syncwarp();
-        if (v && lane == __ffs(peers) - 1) atomicAdd(&S.wcnt[wl][sl >> 1], (uint32_t)__popc(peers) << (16 * (sl & 1)));
-        __syncwarp();
-        if (v) S.sorted[pos] = S.letter[i];
+      // 3. stable placement: cursor of (warp, slot) + rank
+      for (int i = w0 + lane; i < w1; i += 32) {
+        const uint32_t w = P[i];
+        const uint32_t s = (w >> 8) & 1023u;
+        if ((w & PK_OUT) || (dom && s == 0)) continue;
+        S.sorted[S.wc[wl][s] + ((w >> 18) & 1023u)] = (uint8_t)w;
       }
+      if (!ahead && threadIdx.x == 0) { S.ntile = tn; S.ncur = nxt; }
       __syncthreads();
-      // 3. runs: every thread folds an equal piece of the sorted letters; a run
+      // 4. runs: every thread folds an equal piece of the sorted letters; a run
       // inside one piece is finished there, a run across pieces is joined below
       const uint32_t TOT = S.seg[nsl];
-      const uint32_t C = (TOT + nthr - 1) / nthr;
+      const uint32_t C = ((TOT + nthr - 1) / nthr) | 1u;     // odd: the threads' pieces start in distinct banks
       const uint32_t pa = min(TOT, threadIdx.x * C), pz = min(TOT, pa + C);
       if (pa < pz) {
-        int lo = 0, hi = nsl - 1;                 // run containing position pa
+        int lo = 0, hi = nsl - 1;                 // last slot whose run starts at or before pa
         while (lo < hi) {
           const int mid = (lo + hi + 1) >> 1;
           if (S.seg[mid] <= pa) lo = mid; else hi = mid - 1;
@@ -993,8 +1401,8 @@ k_fold(const typename RecT<F>::type* recs, const Tile* units, const unsigned int
               for (uint32_t j = pos; j < end; ++j) V = apply_map(V, S.lmap[S.sorted[j]], ns);
             }
             if (starts && ends) {
-              if (single) finalize_slot<F>(p, fc, S.U, S.T.skey[sl], V, t.bucket);
-              else pool[S.item_off + S.item_cnt + sl] = Pair{S.T.skey[sl], V};
+              if (single) finalize_slot<F>(p, fc, outer_of(S), S.skey[sl], V, t.bucket);
+              else pool[S.item_off + S.item_cnt + sl] = Pair{S.skey[sl], V};
             } else if (!starts) {
               S.firstmap[threadIdx.x] = V;          // continues a run begun in an earlier piece
             } else {
@@ -1006,44 +1414,53 @@ k_fold(const typename RecT<F>::type* recs, const Tile* units, const unsigned int
         }
       }
       __syncthreads();
+      if (!ahead) {
+        // the next unit's records go to L2 while this one is folded
+        ahead = true;
+        if (S.ncur < nun) {
+          const Tile& x = S.ntile;
+          const char* a = (const char*)(recs + x.begin);
+          const char* z = (const char*)(recs + x.end);
+          const char* line = (const char*)((uintptr_t)a & ~(uintptr_t)127) + 128 * (size_t)threadIdx.x;
+          if (line < z) asm volatile("prefetch.L2 [%0];" ::"l"(line));
+          if (line + 128 * nthr < z) asm volatile("prefetch.L2 [%0];" ::"l"(line + 128 * nthr));
+        }
+      }
       // join runs that cross pieces: the piece where a run begins composes the
       // first-run maps of the following pieces in order
       if (pa < pz) {
-        int sl = nsl - 1;
-        {
-          int lo = 0, hi = nsl - 1;               // run containing position pz - 1
-          while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (S.seg[mid] <= pz - 1) lo = mid; else hi = mid - 1;
-          }
-          sl = lo;
+        int lo = 0, hi = nsl - 1;                 // slot of the run holding position pz - 1
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (S.seg[mid] <= pz - 1) lo = mid; else hi = mid - 1;
         }
+        const int sl = lo;
         const uint32_t rs = S.seg[sl], re = S.seg[sl + 1];
         if (re > pz && rs >= pa) {                // my last run begins here and goes on
           uint64_t V = S.lastval[threadIdx.x];
-          const bool st_mode = use_state;          // V holds a state at nibble q0
           for (uint32_t q = threadIdx.x + 1; q < (uint32_t)nthr && q * C < re; ++q) {
             const uint64_t Mq = S.firstmap[q];
-            if (st_mode) {
+            if (use_state) {
               const uint32_t st = step_state((uint32_t)((V >> (4 * p.tab.q0)) & 15ull), Mq);
               V = (uint64_t)st << (4 * p.tab.q0);
             } else {
               V = apply_map(V, Mq, ns);
             }
           }
-          if (single) finalize_slot<F>(p, fc, S.U, S.T.skey[sl], V, t.bucket);
-          else pool[S.item_off + S.item_cnt + sl] = Pair{S.T.skey[sl], V};
+          if (single) finalize_slot<F>(p, fc, outer_of(S), S.skey[sl], V, t.bucket);
+          else pool[S.item_off + S.item_cnt + sl] = Pair{S.skey[sl], V};
         }
       }
-      __syncthreads();
-      // the dominant candidate (slot 0): each thread folds its contiguous piece
-      // of the unit in trace order, pieces are combined in order
+      // the dominant candidate: each thread folds its contiguous piece of the
+      // unit in trace order, pieces are combined in order
       if (dom) {
-        const int c = (len + nthr - 1) / nthr;
+        const int c = ((len + nthr - 1) / nthr) | 1;     // odd: conflict-free reads across the warp
         const int a = min(len, (int)threadIdx.x * c), z = min(len, a + c);
         uint64_t M = IDENTITY_MAP;
-        for (int i = a; i < z; ++i)
-          if (S.slot_of[i] == DOM_SLOT) M = apply_map(M, S.lmap[S.letter[i]], ns);
+        for (int i = a; i < z; ++i) {
+          const uint32_t w = P[i];
+          if ((w & (PK_OUT | (1023u << 8))) == 0) M = apply_map(M, S.lmap[w & 0xFFu], ns);
+        }
         for (int off = 1; off < 32; off <<= 1) {
           const uint64_t o = __shfl_down_sync(FULL, M, off);
           if ((lane & (2 * off - 1)) == 0) M = apply_map(M, o, ns);
@@ -1053,16 +1470,31 @@ k_fold(const typename RecT<F>::type* recs, const Tile* units, const unsigned int
         if (threadIdx.x == 0) {
           uint64_t T = S.wmaps[0];
           for (int w = 1; w < FOLD_WARPS; ++w) T = apply_map(T, S.wmaps[w], ns);
-          if (single) finalize_slot<F>(p, fc, S.U, S.T.skey[0], T, t.bucket);
-          else pool[S.item_off + S.item_cnt + 0] = Pair{S.T.skey[0], T};
+          if (single) finalize_slot<F>(p, fc, outer_of(S), S.skey[0], T, t.bucket);
+          else pool[S.item_off + S.item_cnt + 0] = Pair{S.skey[0], T};
         }
-        __syncthreads();
       }
+      // clear the table entries and counters this pass used
+      for (int s = threadIdx.x; s < nsl; s += nthr) {
+        const uint16_t hp = S.hpos[s];
+        if (hp != NO_POS) {
+          S.tkey[hp] = EMPTY_KEY;
+          if constexpr (!FoldShared<F>::PACKED) S.tslot[hp] = NO_SLOT;
+        }
+        for (int w = 0; w < FOLD_WARPS; ++w) S.wc[w][s] = 0;
+      }
+      __syncthreads();
       if (threadIdx.x == 0) { S.item_cnt += (uint32_t)nsl; S.npass -= 1; }
     }
     __syncthreads();
-    if (single) finalize_outer<F>(p, fc, S.U, t.bucket);
+    if (single) finalize_outer<F>(p, fc, outer_of(S), t.bucket);
     else if (threadIdx.x == 0) items[u] = Item{S.item_off, S.item_cnt, 0};
+    if (threadIdx.x == 0) {
+      // a unit whose first pass overflowed never looked ahead: do it now
+      if (!ahead) { S.ntile = units[nxt < nun ? nxt : nun - 1]; S.ncur = nxt; }
+      S.cur = S.ncur;
+      S.tile = S.ntile;
+    }
   }
   __syncthreads();
   flush_final(p, fc);
@@ -1165,14 +1597,14 @@ k_combine(const Item* items_in, const Pair* pool_in, const Group* groups, const 
       }
       const unsigned int nsl = min(S.T.nslots, (unsigned int)SLOTS);
       for (unsigned int s = threadIdx.x; s < nsl; s += blockDim.x) {
-        if (final_) finalize_slot<F>(p, fc, S.U, S.T.skey[s], S.smap[s], G.bucket);
+        if (final_) finalize_slot<F>(p, fc, &S.U, S.T.skey[s], S.smap[s], G.bucket);
         else pool_out[S.out_off + S.out_cnt + s] = Pair{S.T.skey[s], S.smap[s]};
       }
       __syncthreads();
       if (threadIdx.x == 0) { S.out_cnt += nsl; S.npass -= 1; }
     }
     __syncthreads();
-    if (final_) finalize_outer<F>(p, fc, S.U, G.bucket);
+    if (final_) finalize_outer<F>(p, fc, &S.U, G.bucket);
     else if (threadIdx.x == 0) items_out[g] = Item{S.out_off, S.out_cnt, 0};
   }
   __syncthreads();
@@ -1209,14 +1641,14 @@ __global__ void k_root(const Acc* acc, Params p, uint64_t n, rv_result* out) {
 struct Plan {
   int F, B1, B2, P1, P, G_w, nchunk;
   bool tiled;
-  uint64_t n, per_warp, unit;
+  uint64_t n, per_warp, unit, tile2;
   uint64_t max_tiles2, max_units;
   int levels;
   size_t rec_bytes;
   // workspace offsets
   size_t o_acc, o_hist, o_part, o_tot1, o_bstart1, o_recA, o_recB, o_tiles2, o_tf2, o_tk2, o_hist2, o_tot2,
       o_bstart2, o_units, o_uf, o_uk, o_items0, o_items1, o_groups, o_gf0, o_gk0, o_gf1, o_gk1, o_pool0,
-      o_pool1, o_res, o_hkey, o_hpred, o_hts, total;
+      o_pool1, o_res, o_hkey, o_hpred, o_hts, o_uend, total;
 };
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -1246,8 +1678,9 @@ static Plan make_plan(const rv_formula* f, uint64_t n, int host_input, const rv_
   b2 += extra_b2;
   pl.B2 = std::min(7, std::max(0, b2));
   pl.P = pl.P1 << pl.B2;
-  pl.unit = o && o->unit_records ? (uint64_t)o->unit_records : 8192;
-  pl.unit = std::min<uint64_t>(UNIT_MAX, std::max<uint64_t>(256, pl.unit));
+  const uint64_t unit_max = pl.F == FMT_K32 ? FoldCfg<FMT_K32>::UNIT : FoldCfg<FMT_K64>::UNIT;
+  pl.unit = o && o->unit_records ? (uint64_t)o->unit_records : unit_max;
+  pl.unit = std::min<uint64_t>(unit_max, std::max<uint64_t>(256, pl.unit));
   pl.tiled = pl.B1 == 8;
   const uint64_t max_w = (uint64_t)num_sms() * 3 * SC_WARPS;
   uint64_t gw = (n + 2047) / 2048;
@@ -1262,7 +1695,8 @@ static Plan make_plan(const rv_formula* f, uint64_t n, int host_input, const rv_
     pl.G_w = (int)std::max<uint64_t>(1, (n + pl.per_warp - 1) / pl.per_warp);
   }
   pl.nchunk = (pl.G_w + COLCHUNK - 1) / COLCHUNK;
-  pl.max_tiles2 = n / TILE2 + pl.P1 + 1;
+  pl.tile2 = pl.F == FMT_K32 ? Tile2Len<FMT_K32>::v : Tile2Len<FMT_K64>::v;
+  pl.max_tiles2 = n / pl.tile2 + pl.P1 + 1;
   pl.max_units = n / pl.unit + pl.P + 1;
   pl.levels = 0;
   for (uint64_t cap = 1; cap < n / pl.unit + 2; cap *= GC) ++pl.levels;
@@ -1285,6 +1719,7 @@ static Plan make_plan(const rv_formula* f, uint64_t n, int host_input, const rv_
   pl.o_units = take(pl.max_units * sizeof(Tile));
   pl.o_uf = take((size_t)pl.P * 4);
   pl.o_uk = take((size_t)pl.P * 4);
+  pl.o_uend = take((size_t)pl.P * 8);
   pl.o_items0 = take(pl.max_units * sizeof(Item));
   pl.o_items1 = take(pl.max_units * sizeof(Item));
   pl.o_groups = take(pl.max_units * sizeof(Group));
@@ -1372,14 +1807,19 @@ static rv_status launch_all(const Plan& pl, const rv_formula* f, const void* key
       uint64_t* tot2 = (uint64_t*)(ws + pl.o_tot2);
       uint64_t* bstart2 = (uint64_t*)(ws + pl.o_bstart2);
       Rec* recB = (Rec*)(ws + pl.o_recB);
-      RV_LAUNCH("k_count_tiles", k_count_tiles, (pl.P1 + 255) / 256, 256, 0, s, bstart1, pl.P1, (uint64_t)TILE2, tk2);
+      RV_LAUNCH("k_count_tiles", k_count_tiles, (pl.P1 + 255) / 256, 256, 0, s, bstart1, pl.P1, pl.tile2, tk2);
       RV_LAUNCH("k_scan_u32", k_scan_u32, 1, 1024, 0, s, tk2, pl.P1, tf2, &acc->n_tiles2);
-      RV_LAUNCH("k_emit_tiles", k_emit_tiles, (int)((pl.max_tiles2 + 255) / 256), 256, 0, s, bstart1, pl.P1, (uint64_t)TILE2, tf2, tk2, &acc->n_tiles2, tiles2);
+      RV_LAUNCH("k_emit_tiles", k_emit_tiles, (int)((pl.max_tiles2 + 255) / 256), 256, 0, s, bstart1, pl.P1, pl.tile2, tf2, tk2, &acc->n_tiles2, tiles2);
       const int t2_blocks = (int)((pl.max_tiles2 + SC_WARPS - 1) / SC_WARPS);
       RV_LAUNCH("k_hist2", k_hist2<F>, t2_blocks, SC_WARPS * 32, 0, s, recA, tiles2, &acc->n_tiles2, pl.B1, pl.B2, hist2);
       RV_LAUNCH("k_scan2", k_scan2, (pl.P + 255) / 256, 256, 0, s, hist2, tf2, tk2, pl.P1, pl.B2, tot2);
       RV_LAUNCH("k_bucket_scan", k_bucket_scan, 1, 1024, 0, s, tot2, pl.P, bstart2);
-      RV_LAUNCH("k_scatter2", k_scatter2<F>, t2_blocks, SC_WARPS * 32, 0, s, recA, tiles2, &acc->n_tiles2, pl.B1, pl.B2, hist2, bstart2, recB);
+      if (F == FMT_K32)
+        RV_LAUNCH("k_scatter2", k_scatter2<F>, t2_blocks, SC_WARPS * 32, 0, s, recA, tiles2, &acc->n_tiles2, pl.B1, pl.B2, hist2,
+                  bstart2, recB);
+      else
+        RV_LAUNCH("k_scatter2_tile", k_scatter2_tile<F>, (int)pl.max_tiles2, TB_THREADS, sizeof(Tile2Shared<F>), s, recA, tiles2,
+                  &acc->n_tiles2, pl.B1, pl.B2, hist2, bstart2, recB);
       recs = recB;
       bstart = bstart2;
     }
@@ -1391,11 +1831,13 @@ static rv_status launch_all(const Plan& pl, const rv_formula* f, const void* key
     Group* groups = (Group*)(ws + pl.o_groups);
     Pair* pool0 = (Pair*)(ws + pl.o_pool0);
     Pair* pool1 = (Pair*)(ws + pl.o_pool1);
-    RV_LAUNCH("k_count_tiles", k_count_tiles, (pl.P + 255) / 256, 256, 0, s, bstart, pl.P, pl.unit, uk);
+    uint64_t* uend = (uint64_t*)(ws + pl.o_uend);
+    RV_LAUNCH("k_count_units", k_count_units, (pl.P + 255) / 256, 256, 0, s, bstart, pl.P, pl.B2, pl.unit, F != FMT_K2 ? 1 : 0, uk, uend);
     RV_LAUNCH("k_scan_u32", k_scan_u32, 1, 1024, 0, s, uk, pl.P, uf, &acc->n_units);
-    RV_LAUNCH("k_emit_tiles", k_emit_tiles, (int)((pl.max_units + 255) / 256), 256, 0, s, bstart, pl.P, pl.unit, uf, uk, &acc->n_units, units);
-    const int grid = (int)std::min<uint64_t>(pl.max_units, (uint64_t)num_sms() * 2);
-    RV_LAUNCH("k_fold", k_fold<F>, grid, FOLD_THREADS, sizeof(FoldShared), s, recs, units, &acc->n_units, p, items0, pool0);
+    RV_LAUNCH("k_emit_tiles", k_emit_tiles, (int)((pl.max_units + 255) / 256), 256, 0, s, bstart, pl.P, pl.unit, uf, uk, &acc->n_units, units,
+              F != FMT_K2 ? uend : nullptr);
+    const int grid = (int)std::min<uint64_t>(pl.max_units, (uint64_t)num_sms() * FoldCfg<F>::MINB);
+    RV_LAUNCH("k_fold", k_fold<F>, grid, FOLD_THREADS, sizeof(FoldShared<F>), s, recs, units, &acc->n_units, p, items0, pool0);
     const uint32_t* fin = uf;
     const uint32_t* kin = uk;
     uint32_t* gf[2] = {(uint32_t*)(ws + pl.o_gf0), (uint32_t*)(ws + pl.o_gf1)};
@@ -1429,11 +1871,12 @@ static bool g_attr_done[3];
 template <int F>
 static rv_status set_attrs() {
   if (g_attr_done[F]) return RV_OK;
-  RV_CU(cudaFuncSetAttribute(k_fold<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(FoldShared)));
+  RV_CU(cudaFuncSetAttribute(k_fold<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(FoldShared<F>)));
   RV_CU(cudaFuncSetAttribute(k_combine<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(CombineShared)));
   RV_CU(cudaFuncSetAttribute(k_hist<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, SC_WARPS * 2048 * 4));
   RV_CU(cudaFuncSetAttribute(k_scatter<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, SC_WARPS * 2048 * 4));
   RV_CU(cudaFuncSetAttribute(k_scatter_tile<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TileShared<F>)));
+  RV_CU(cudaFuncSetAttribute(k_scatter2_tile<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Tile2Shared<F>)));
   g_attr_done[F] = true;
   return RV_OK;
 }
