@@ -2,22 +2,23 @@
 // (Algorithm 1, Sec. 4.2: SortTrace -> SpawnMonitors -> Distribute ->
 // ApplyQuantifiers), re-designed for B300.
 //
-// map      k_hist / k_colscan_* / k_bucket_scan / k_scatter: a stable
-//          multisplit of the events into 2^B1 buckets by the top bits of the
-//          mixed outer key (optionally a second split k_hist2 / k_scan2 /
-//          k_scatter2 into 2^B2 sub-buckets).  Each warp owns a contiguous
-//          super-tile of the trace and private bucket cursors, so records keep
-//          trace order inside every bucket; a record is the letter plus the
-//          key bits the bucket does not imply (4 or 8 bytes).
-// monitor  k_fold: one CTA folds a unit (<= unit_records records of a bucket).
-//          Warps take contiguous slices of the unit; each key (binding) gets a
-//          slot in a shared-memory hash table and every warp composes the
-//          64-bit transition maps of its slice's letters per slot (equal keys
-//          inside a 32-record round are grouped by a ballot match and
-//          applied in lane order).  The warps' maps are then composed in
-//          order.  This is the per-cluster monitor of ProcessBuffer, with
-//          the long clusters of a Zipf head split across warps and CTAs and
-//          rejoined by associativity of map composition.
+// map      a stable two-level multisplit of the events by the mixed outer key.
+//          Level 1 (k_hist_tile / column scans / k_scatter_tile): CTA tiles of
+//          the trace are counting-sorted by the top 8 key bits in shared memory
+//          and each bucket's run is written out contiguously.  Level 2
+//          (k_hist2 / k_scan2 / k_scatter2 or k_scatter2_tile): tiles of every
+//          first-level bucket are split again by the next B2 bits.  Trace order
+//          is kept inside every bucket; a record is the letter plus the key
+//          bits the bucket does not imply (4 or 8 bytes).
+// monitor  k_fold: one CTA folds a unit -- a piece of a large bucket, or whole
+//          small buckets of one first-level bucket.  Each binding (key) takes a
+//          slot in a shared-memory table; every record gets its rank among its
+//          slot's records in its warp's slice; one scan and a placement group
+//          the letters by binding in trace order; the runs are folded by the
+//          LTL4 Moore monitor (plain state steps from q0, or 4-bit-per-state
+//          transition maps composed by byte permutes where a run starts
+//          elsewhere).  A binding that fills at least half of the unit (a Zipf
+//          head) is folded in place instead of being sorted.
 // reduce   a bucket held by one unit is finalised in k_fold; buckets split
 //          over several units pass (key, map) pairs to k_combine, which
 //          composes them level by level in unit order (fan-in 16) and
@@ -1113,22 +1114,13 @@ __device__ __noinline__ int fold_insert(FoldShared<F>& S, uint64_t key, Acc* acc
   return -1;
 }
 
-// Slot of every lane's key: one probe per lane, then the keys still absent are
-// inserted one distinct key at a time (lanes holding the same new key share
-// the insertion).
+// Slot of every lane's key: a probe, then an insertion for keys not yet in
+// the table.  Lanes insert in parallel; lanes holding the same new key meet
+// at the entry the first of them claimed and wait for its slot.
 template <int F>
 __device__ __forceinline__ int warp_slot(FoldShared<F>& S, uint64_t key, bool want, Acc* acc) {
   int slot = want ? fold_probe<F>(S, key, acc) : -1;
-  uint32_t need = __ballot_sync(FULL, slot == PROBE_NEED);
-  while (need) {
-    const int ld = __ffs(need) - 1;
-    const uint64_t k = __shfl_sync(FULL, key, ld);
-    int s = 0;
-    if ((int)(threadIdx.x & 31) == ld) s = fold_insert<F>(S, key, acc);
-    s = __shfl_sync(FULL, s, ld);
-    if (slot == PROBE_NEED && key == k) slot = s;
-    need = __ballot_sync(FULL, slot == PROBE_NEED);
-  }
+  if (slot == PROBE_NEED) slot = fold_insert<F>(S, key, acc);
   return slot;
 }
 
