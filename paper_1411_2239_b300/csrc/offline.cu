@@ -81,17 +81,6 @@ __device__ __forceinline__ uint32_t match_bits(uint32_t v, bool valid) {
   return m;
 }
 
-// the same with a runtime number of bits (values below 2^nbits)
-__device__ __forceinline__ uint32_t match_nbits(uint32_t v, bool valid, int nbits) {
-  const uint32_t vb = __ballot_sync(FULL, valid);
-  uint32_t m = valid ? vb : ~vb;
-  for (int k = 0; k < nbits; ++k) {
-    const uint32_t bk = __ballot_sync(FULL, (v >> k) & 1u);
-    m &= ((v >> k) & 1u) ? bk : ~bk;
-  }
-  return m;
-}
-
 template <int F>
 __device__ __forceinline__ uint64_t load_key(const void* p, uint64_t i) {
   if (F == FMT_K32) return ((const uint32_t*)p)[i];
@@ -182,10 +171,9 @@ k_hist_tile(const void* keyp, const uint32_t* ts, uint64_t n, int nq, uint32_t* 
 
 template <int F>
 struct TileShared {
-  typename RecT<F>::type srec[TileSize<F>::v];
-  typename RecT<F>::type orec[TileSize<F>::v];
-  uint8_t sb[TileSize<F>::v];
-  uint8_t ob[TileSize<F>::v];
+  typename RecT<F>::type srec[TileSize<F>::v];   // the tile's records in trace order
+  uint8_t sb[TileSize<F>::v];                    // bucket of srec[i]
+  uint16_t perm[TileSize<F>::v];                 // perm[j]: record at position j of the bucket order
   uint32_t wcur[TB_WARPS][256];
   uint32_t loc[256];
   uint64_t gbase[256];
@@ -193,7 +181,7 @@ struct TileShared {
 };
 
 template <int F>
-__global__ void __launch_bounds__(TB_THREADS)
+__global__ void __launch_bounds__(TB_THREADS, 3)
 k_scatter_tile(const void* keyp, const uint8_t* pred, uint64_t n, int nq, int n_letters, const uint32_t* pre,
                const uint64_t* bstart, typename RecT<F>::type* out, Acc* acc) {
   typedef typename RecT<F>::type Rec;
@@ -264,23 +252,22 @@ k_scatter_tile(const void* keyp, const uint8_t* pred, uint64_t n, int nq, int n_
     __syncwarp();
     if (v && lane == __ffs(peers) - 1) S.wcur[wl][b] += __popc(peers);
     __syncwarp();
-    if (v) { S.orec[pos] = S.srec[i]; S.ob[pos] = (uint8_t)b; }
+    if (v) S.perm[pos] = (uint16_t)i;
   }
   __syncthreads();
-  // 5. runs of each bucket go out contiguously
-  for (int i = threadIdx.x; i < len; i += TB_THREADS) {
-    const uint32_t b = S.ob[i];
-    out[S.gbase[b] + (i - S.loc[b])] = S.orec[i];
+  // 5. runs of each bucket go out contiguously, gathered through perm
+  for (int j = threadIdx.x; j < len; j += TB_THREADS) {
+    const uint32_t i = S.perm[j], b = S.sb[i];
+    out[S.gbase[b] + (j - S.loc[b])] = S.srec[i];
   }
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&acc->err, ERR_LETTER);
 }
 
 // Rank of each lane's bucket b among the records of its warp so far: lanes of
-// equal buckets are matched by ballots and the lowest of them advances the
-// warp's counter (equal buckets never share a leader, so no atomics).
-template <int BITS>
+// equal buckets are matched and the lowest of them advances the warp's
+// counter (equal buckets never share a leader, so no atomics).
 __device__ __forceinline__ uint32_t warp_rank(uint32_t b, bool v, uint32_t* cnt, uint32_t lt) {
-  const uint32_t peers = match_bits<BITS>(b, v);
+  const uint32_t peers = __match_any_sync(FULL, v ? b : 0xFFFFFFFFu);
   const int ld = __ffs(peers) - 1;
   uint32_t old = 0;
   if (v && (int)(threadIdx.x & 31) == ld) {
@@ -623,7 +610,7 @@ k_scatter2(const typename RecT<F>::type* in, const Tile* tiles, const unsigned i
 #pragma unroll
     for (int j = 0; j < BATCH; ++j) {
       const bool v = b[j] != 0xFFFFFFFFu;
-      const uint32_t peers = match_bits<7>(b[j], v);
+      const uint32_t peers = __match_any_sync(FULL, v ? b[j] : 0xFFFFFFFFu);
       uint32_t pos = 0;
       if (v) pos = cur[b[j]] + __popc(peers & lt);
       __syncwarp();
@@ -681,7 +668,7 @@ k_scatter2_tile(const typename RecT<F>::type* in, const Tile* tiles, const unsig
     const int i = w0 + j * 32 + lane;
     const bool v = i < len;
     const uint32_t b = (uint32_t)((uint64_t)rec[j] >> sh) & (uint32_t)(P2 - 1);
-    const uint32_t rank = warp_rank<7>(b, v, S.wcur[wl], lt);
+    const uint32_t rank = warp_rank(b, v, S.wcur[wl], lt);
     if (v) S.ibr[i] = b | (rank << 8);
   }
   __syncthreads();
@@ -1013,6 +1000,8 @@ struct FoldShared {
 
 // MINB CTAs per SM must fit the SM's 228 KB of shared memory (1 KB of it reserved per CTA)
 static_assert(FoldCfg<FMT_K32>::MINB * (sizeof(FoldShared<FMT_K32>) + 1024) <= 228 * 1024, "fold CTAs per SM");
+static_assert(3 * (sizeof(TileShared<FMT_K32>) + 1024) <= 228 * 1024, "three level-1 tiles per SM");
+static_assert(3 * (sizeof(TileShared<FMT_K64>) + 1024) <= 228 * 1024, "three level-1 tiles per SM");
 static_assert(FoldCfg<FMT_K64>::MINB * (sizeof(FoldShared<FMT_K64>) + 1024) <= 228 * 1024, "fold CTAs per SM");
 static_assert(FoldCfg<FMT_K2>::MINB * (sizeof(FoldShared<FMT_K2>) + 1024) <= 228 * 1024, "fold CTAs per SM");
 
@@ -1285,8 +1274,7 @@ k_fold(const typename RecT<F>::type* recs, const Tile* units, const unsigned int
           int slot = warp_slot<F>(S, key, in && !is_cand, p.acc);
           if (is_cand) slot = 0;
           const bool v = slot >= 0;
-          const uint32_t mx = __reduce_max_sync(FULL, v ? (uint32_t)slot : 0u);
-          const uint32_t peers = match_nbits(v ? (uint32_t)slot : 0u, v, mx ? 32 - __clz(mx) : 0);
+          const uint32_t peers = __match_any_sync(FULL, v ? (uint32_t)slot : 0xFFFFFFFFu);
           const int ld = __ffs(peers) - 1;
           uint32_t old = 0;
           if (v && lane == ld) {
