@@ -465,6 +465,10 @@ def run_serve(args):
     codes = synth.FILE_CODES
     streams_data = [synth.file_trace(w["events_per_stream"], w["users"], 1_000_000, seed=1000 * w["cfg"] + i)
                     for i in range(w["streams"])]
+    # a stream replays its trace cyclically; its first 1M events are appended
+    # so that every chunk (at most 1M events) is one contiguous slice
+    ext = [(np.concatenate([tr.key, tr.key[:1 << 20]]), np.concatenate([tr.pred, tr.pred[:1 << 20]]), tr.n)
+           for tr in streams_data]
     f = rv.Formula(w["formula"], codes, key_bits=64)
     svc = rv.Service(f, max_bindings=1 << 25, max_outer=1 << 21, max_batch_events=1 << 23,
                      max_staged_events=1 << 26, max_streams=w["streams"])
@@ -497,11 +501,10 @@ def run_serve(args):
         t_next += rng.exponential(1.0 / chunk_rate)
         i = int(rng.integers(w["streams"]))
         sz = int(np.exp(rng.uniform(np.log(4096), np.log(1 << 20))))
-        tr = streams_data[i]
-        a = pos[i] % tr.n
-        sz = min(sz, tr.n - a)          # contiguous slice (a view); the stream wraps on the next chunk
+        ekey, epred, tn = ext[i]
+        a = pos[i] % tn
         try:
-            sts[i].push(tr.key[a:a + sz], tr.pred[a:a + sz])
+            sts[i].push(ekey[a:a + sz], epred[a:a + sz])
             pushed[i].append(sz)
             pos[i] += sz
             events += sz

@@ -382,9 +382,19 @@ k_bfold(BatchDev d, const uint64_t* recs, const uint64_t* bstart, unsigned long 
         for (uint32_t base = lo; base < hi; base += 32) {
           const uint32_t n = min(32u, hi - base);
           const uint32_t mine = lane < n ? S.sorted[base + lane] : 0u;
-          for (uint32_t j = 0; j < n; ++j) {
-            const uint32_t l = __shfl_sync(FULL, mine, j);
-            st = (uint32_t)((S.lmap[l][lane] >> (4 * st)) & 15ull);
+          if (n == 32) {
+            // a full round: the maps do not depend on the state, so all 32
+            // are fetched ahead and only the shift-and-mask chain is serial
+#pragma unroll
+            for (int j0 = 0; j0 < 32; j0 += 8) {
+              uint64_t m[8];
+#pragma unroll
+              for (int j = 0; j < 8; ++j) m[j] = S.lmap[__shfl_sync(FULL, mine, j0 + j)][lane];
+#pragma unroll
+              for (int j = 0; j < 8; ++j) st = step_state(st, m[j]);
+            }
+          } else {
+            for (uint32_t j = 0; j < n; ++j) st = step_state(st, S.lmap[__shfl_sync(FULL, mine, j)][lane]);
           }
         }
         S.state[sl][lane] = (uint8_t)st;
