@@ -1011,8 +1011,11 @@ __device__ __forceinline__ OuterTable* outer_of(FoldShared<F>& S) {
   else return nullptr;
 }
 
+// a binding key inside a bucket: 24 bits for one 32-bit key, 56 otherwise
+template <int F> using FKey = typename std::conditional<F == FMT_K32, uint32_t, uint64_t>::type;
+
 template <int F>
-__device__ __forceinline__ uint32_t fold_home(uint64_t key) {
+__device__ __forceinline__ uint32_t fold_home(FKey<F> key) {
   // the low bits of a mixed key are uniform; a two-variable key carries the
   // raw inner value there, so it is hashed again
   if constexpr (F == FMT_K2) return (uint32_t)(key_mult(key) >> (64 - FoldCfg<F>::HTB));
@@ -1047,15 +1050,15 @@ __device__ __forceinline__ int fold_entry_slot(FoldShared<F>& S, uint32_t h, uin
 }
 
 template <int F>
-__device__ __forceinline__ bool fold_key_is(uint64_t e, uint64_t key) {
-  if constexpr (FoldShared<F>::PACKED) return (e >> 32) == key;
+__device__ __forceinline__ bool fold_key_is(uint64_t e, FKey<F> key) {
+  if constexpr (FoldShared<F>::PACKED) return (uint32_t)(e >> 32) == key;
   else return e == key;
 }
 
 // Lookup without insertion: the slot of key, PROBE_NEED, or -1 (table full or
 // a bounded wait gave up).
 template <int F>
-__device__ __forceinline__ int fold_probe(FoldShared<F>& S, uint64_t key, Acc* acc) {
+__device__ __forceinline__ int fold_probe(FoldShared<F>& S, FKey<F> key, Acc* acc) {
   constexpr int HT = FoldShared<F>::HT;
   uint32_t h = fold_home<F>(key);
   volatile uint64_t* vk = S.tkey;
@@ -1073,7 +1076,7 @@ __device__ __forceinline__ int fold_probe(FoldShared<F>& S, uint64_t key, Acc* a
 // taken and published; lanes that meet the claimed entry wait for it.
 // Returns -1 when the slot table is full (the pass then restarts split).
 template <int F>
-__device__ __noinline__ int fold_insert(FoldShared<F>& S, uint64_t key, Acc* acc) {
+__device__ __noinline__ int fold_insert(FoldShared<F>& S, FKey<F> key, Acc* acc) {
   constexpr int HT = FoldShared<F>::HT, SL = FoldShared<F>::SL;
   constexpr bool PK = FoldShared<F>::PACKED;
   uint32_t h = fold_home<F>(key);
@@ -1081,7 +1084,7 @@ __device__ __noinline__ int fold_insert(FoldShared<F>& S, uint64_t key, Acc* acc
   for (int probe = 0; probe < HT; ++probe) {
     uint64_t e = vk[h];
     if (e == EMPTY_KEY) {
-      const uint64_t claim = PK ? (key << 32) | E_PENDING : key;
+      const uint64_t claim = PK ? ((uint64_t)key << 32) | E_PENDING : (uint64_t)key;
       const unsigned long long prev = atomicCAS((unsigned long long*)&S.tkey[h], (unsigned long long)EMPTY_KEY,
                                                 (unsigned long long)claim);
       if (prev == EMPTY_KEY) {
@@ -1090,7 +1093,7 @@ __device__ __noinline__ int fold_insert(FoldShared<F>& S, uint64_t key, Acc* acc
         if (full) S.ovf = 1;
         else { S.skey[s] = key; S.hpos[s] = (uint16_t)h; }
         __threadfence_block();
-        if constexpr (PK) vk[h] = (key << 32) | (full ? E_FULL : s);
+        if constexpr (PK) vk[h] = ((uint64_t)key << 32) | (full ? E_FULL : s);
         else *(volatile uint16_t*)&S.tslot[h] = full ? FULL_SLOT : (uint16_t)s;
         return full ? -1 : (int)s;
       }
@@ -1107,7 +1110,7 @@ __device__ __noinline__ int fold_insert(FoldShared<F>& S, uint64_t key, Acc* acc
 // the table.  Lanes insert in parallel; lanes holding the same new key meet
 // at the entry the first of them claimed and wait for its slot.
 template <int F>
-__device__ __forceinline__ int warp_slot(FoldShared<F>& S, uint64_t key, bool want, Acc* acc) {
+__device__ __forceinline__ int warp_slot(FoldShared<F>& S, FKey<F> key, bool want, Acc* acc) {
   int slot = want ? fold_probe<F>(S, key, acc) : -1;
   if (slot == PROBE_NEED) slot = fold_insert<F>(S, key, acc);
   return slot;
@@ -1209,7 +1212,7 @@ k_fold(const typename RecT<F>::type* recs, const Tile* units, const unsigned int
     const char* ra16 = (const char*)((uintptr_t)ra & ~(uintptr_t)15);
     const uint32_t rbytes = (uint32_t)((((uintptr_t)(recs + t.end) + 15) & ~(uintptr_t)15) - (uintptr_t)ra16);
     uint32_t* P = S.pk + (BULK ? (ra - ra16) / 4 : 0);   // fold word of record i: P[i]
-    uint64_t cand = BULK ? 0 : (uint64_t)recs[t.begin] >> 8;
+    FKey<F> cand = BULK ? 0 : (FKey<F>)((uint64_t)recs[t.begin] >> 8);
     while (true) {
       __syncthreads();
       if (S.npass == 0) break;
@@ -1223,7 +1226,7 @@ k_fold(const typename RecT<F>::type* recs, const Tile* units, const unsigned int
         }
         if (!mbar_wait(&S.mbar, bulk_phase)) atomicOr(&S.bad, 1u);
         bulk_phase ^= 1u;
-        cand = P[0] >> 8;
+        cand = (FKey<F>)(P[0] >> 8);
       }
       const bool cand_in = in_pass(cand, bits, val);
       if (threadIdx.x == 0) {
@@ -1255,7 +1258,7 @@ k_fold(const typename RecT<F>::type* recs, const Tile* units, const unsigned int
           if (base + j * 32 >= w1) break;                  // warp-uniform
           const int i = base + j * 32 + lane;
           const bool valid = i < w1;
-          const uint64_t key = (uint64_t)r[j] >> 8;
+          const FKey<F> key = (FKey<F>)((uint64_t)r[j] >> 8);
           const uint32_t letter = (uint32_t)r[j] & 0xFFu;
           const bool in = valid && in_pass(key, bits, val);
           const bool is_cand = in && cand_in && key == cand;

@@ -201,3 +201,40 @@ def test_repeatable(rv, torch_cuda):
     r = [rv.verify(f, k, p, want_bindings=True) for _ in range(3)]
     assert r[0].bindings == r[1].bindings == r[2].bindings
     assert r[0].outer == r[1].outer == r[2].outer
+
+
+def _fmix32(x):
+    """MurmurHash3's 32-bit finaliser (public domain), the published mix the
+    library applies to a 32-bit key before taking bucket bits from its top."""
+    x = x.astype(np.uint64)
+    x ^= x >> np.uint64(16)
+    x = (x * np.uint64(0x85EBCA6B)) & np.uint64(0xFFFFFFFF)
+    x ^= x >> np.uint64(13)
+    x = (x * np.uint64(0xC2B2AE35)) & np.uint64(0xFFFFFFFF)
+    x ^= x >> np.uint64(16)
+    return x.astype(np.uint32)
+
+
+def test_units_that_open_with_one_binding(rv, torch_cuda):
+    # 20 keys chosen to share one bucket (equal top 15 bits of the mixed key),
+    # cut into 256-record units that each open with a burst of one key: units
+    # whose first round is mostly one binding, whatever the rest holds
+    rng = np.random.default_rng(21)
+    cand = rng.integers(0, 2**32, size=4_000_000, dtype=np.uint64).astype(np.uint32)
+    top = _fmix32(cand) >> np.uint32(17)
+    vals, counts = np.unique(top, return_counts=True)
+    same = np.unique(cand[top == vals[np.argmax(counts)]])[:20]
+    assert len(same) == 20
+    heavy, light = same[0], same[1:]
+    blocks = []
+    for u in range(60):
+        share = [0.9, 0.5, 0.2][u % 3]            # dominated, balanced and light units
+        body = np.where(rng.random(228) < share, heavy, rng.choice(light, size=228))
+        blocks.append(np.concatenate([np.full(28, heavy, dtype=np.uint32), body.astype(np.uint32)]))
+    key = np.concatenate(blocks)
+    noise = rng.integers(0, 2**32, size=5000, dtype=np.uint64).astype(np.uint32)
+    key = np.insert(key, rng.integers(0, len(key), size=len(noise)), noise)
+    pred = rng.integers(0, 3, size=len(key)).astype(np.uint8)
+    opts = {"bucket_bits": 8, "sub_bucket_bits": 7, "unit_records": 256}
+    for body in ["G(receive -> F respond)", "F(receive && X respond)", "(receive U respond) || F socket"]:
+        _check(rv, torch_cuda, f"A_{{>=0.5}} x: p(x) => {body}", synth.SOCKET_CODES, key, pred, opts=opts)
