@@ -47,7 +47,7 @@ constexpr int SLOTS = 1024;
 constexpr int HT_BITS = 11;
 constexpr int HT_CAP = 1 << HT_BITS;
 constexpr int UCAP = 256;
-constexpr int GC = 16;
+constexpr int GC = 16;      // items (units or groups) combined by one CTA per level
 constexpr int COLCHUNK = 64;
 constexpr uint16_t NO_SLOT = 0xFFFF;
 constexpr uint16_t FULL_SLOT = 0xFFFE;
@@ -557,30 +557,38 @@ k_hist2(const typename RecT<F>::type* recs, const Tile* tiles, const unsigned in
   for (int b = lane; b < P2; b += 32) hist2[(uint64_t)tile * P2 + b] = cnt[b];
 }
 
-// per (first-level bucket, sub-bucket): exclusive prefix over the bucket's tiles
-__global__ void k_scan2(uint32_t* hist2, const uint32_t* tfirst, const uint32_t* tK, int P1, int B2, uint64_t* tot2) {
+// per (first-level bucket, sub-bucket): exclusive prefix over the bucket's
+// tiles.  One CTA per first-level bucket: SCAN_ROWS rows of threads each take
+// a contiguous share of the tiles for every sub-bucket column, the rows' sums
+// are scanned in shared memory, then every row writes its share's prefixes.
+constexpr int SCAN_ROWS = 8;
+__global__ void __launch_bounds__(128 * SCAN_ROWS)
+k_scan2(uint32_t* hist2, const uint32_t* tfirst, const uint32_t* tK, int P1, int B2, uint64_t* tot2) {
+  __shared__ uint64_t part[SCAN_ROWS][128];
   const int P2 = 1 << B2;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= P1 * P2) return;
-  const int b1 = t >> B2, b2 = t & (P2 - 1);
+  const int b1 = blockIdx.x;
+  const int col = threadIdx.x & 127, row = threadIdx.x >> 7;
   const uint32_t f = tfirst[b1], k = tK[b1];
+  const uint32_t share = (k + SCAN_ROWS - 1) / SCAN_ROWS;
+  const uint32_t j0 = min(k, row * share), j1 = min(k, j0 + share);
+  uint64_t sum = 0;
+  if (col < P2)
+    for (uint32_t j = j0; j < j1; ++j) sum += hist2[(uint64_t)(f + j) * P2 + col];
+  part[row][col] = sum;
+  __syncthreads();
   uint64_t run = 0;
-  constexpr int R = 16;   // rows loaded together, so their latencies overlap
-  for (uint32_t j0 = 0; j0 < k; j0 += R) {
-    uint32_t x[R];
-#pragma unroll
-    for (int j = 0; j < R; ++j) x[j] = j0 + j < k ? hist2[(uint64_t)(f + j0 + j) * P2 + b2] : 0u;
-#pragma unroll
-    for (int j = 0; j < R; ++j) {
-      if (j0 + j < k) hist2[(uint64_t)(f + j0 + j) * P2 + b2] = (uint32_t)run;
-      run += x[j];
+  for (int r = 0; r < row; ++r) run += part[r][col];
+  if (col < P2) {
+    for (uint32_t j = j0; j < j1; ++j) {
+      const uint64_t idx = (uint64_t)(f + j) * P2 + col;
+      const uint32_t x = hist2[idx];
+      hist2[idx] = (uint32_t)run;
+      run += x;
     }
+    if (row == SCAN_ROWS - 1) tot2[(b1 << B2) + col] = run;
   }
-  tot2[t] = run;
 }
 
-// Level-2 split of 32-bit records, one warp per tile: each warp keeps
-// private sub-bucket cursors and writes every record directly.
 template <int F>
 __global__ void __launch_bounds__(SC_WARPS * 32)
 k_scatter2(const typename RecT<F>::type* in, const Tile* tiles, const unsigned int* n_tiles, int B1, int B2,
@@ -1795,7 +1803,7 @@ static rv_status launch_all(const Plan& pl, const rv_formula* f, const void* key
       RV_LAUNCH("k_emit_tiles", k_emit_tiles, (int)((pl.max_tiles2 + 255) / 256), 256, 0, s, bstart1, pl.P1, pl.tile2, tf2, tk2, &acc->n_tiles2, tiles2);
       const int t2_blocks = (int)((pl.max_tiles2 + SC_WARPS - 1) / SC_WARPS);
       RV_LAUNCH("k_hist2", k_hist2<F>, t2_blocks, SC_WARPS * 32, 0, s, recA, tiles2, &acc->n_tiles2, pl.B1, pl.B2, hist2);
-      RV_LAUNCH("k_scan2", k_scan2, (pl.P + 255) / 256, 256, 0, s, hist2, tf2, tk2, pl.P1, pl.B2, tot2);
+      RV_LAUNCH("k_scan2", k_scan2, pl.P1, 128 * SCAN_ROWS, 0, s, hist2, tf2, tk2, pl.P1, pl.B2, tot2);
       RV_LAUNCH("k_bucket_scan", k_bucket_scan, 1, 1024, 0, s, tot2, pl.P, bstart2);
       if (F == FMT_K32)
         RV_LAUNCH("k_scatter2", k_scatter2<F>, t2_blocks, SC_WARPS * 32, 0, s, recA, tiles2, &acc->n_tiles2, pl.B1, pl.B2, hist2,
