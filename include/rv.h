@@ -150,6 +150,8 @@ typedef struct {
   int bucket_bits;       /* log2 of the first-level key buckets, 8..11 */
   int sub_bucket_bits;   /* log2 of the second-level split, 0..7 */
   int unit_records;      /* records folded by one CTA, multiple of 256 */
+  int no_heavy;          /* nonzero: no own sub-buckets for bindings that a sample of
+                            the trace shows to be heavy (one-variable formulas) */
 } rv_verify_opts;
 
 /* Device memory the offline path needs for a trace of n events

@@ -9,7 +9,9 @@
 //          (k_hist2 / k_scan2 / k_scatter2 or k_scatter2_tile): tiles of every
 //          first-level bucket are split again by the next B2 bits.  Trace order
 //          is kept inside every bucket; a record is the letter plus the key
-//          bits the bucket does not imply (4 or 8 bytes).
+//          bits the bucket does not imply (4 or 8 bytes).  Heavy bindings of a
+//          one-variable formula (found by k_hsample / k_hpick on a sample of
+//          the trace) get second-level sub-buckets of their own.
 // monitor  k_fold: one CTA folds a unit -- a piece of a large bucket, or whole
 //          small buckets of one first-level bucket.  Each binding (key) takes a
 //          slot in a shared-memory table; every record gets its rank among its
@@ -18,7 +20,8 @@
 //          LTL4 Moore monitor (plain state steps from q0, or 4-bit-per-state
 //          transition maps composed by byte permutes where a run starts
 //          elsewhere).  A binding that fills at least half of the unit (a Zipf
-//          head) is folded in place instead of being sorted.
+//          head) is folded in place instead of being sorted, and a heavy
+//          binding's own sub-bucket is folded in place with no grouping at all.
 // reduce   a bucket held by one unit is finalised in k_fold; buckets split
 //          over several units pass (key, map) pairs to k_combine, which
 //          composes them level by level in unit order (fan-in 16) and
@@ -55,6 +58,7 @@ constexpr uint64_t EMPTY_KEY = ~0ull;
 constexpr unsigned FULL = 0xFFFFFFFFu;
 constexpr int SPIN_LIMIT = 1 << 22;
 constexpr int BATCH = 16;      // rounds of 32 events whose loads are issued together
+constexpr int HBATCH = 8;      // the same for the level-2 histogram, which keeps more warps resident
 
 struct Tile { uint32_t bucket, k, K, pad; uint64_t begin, end; };
 struct Item { uint64_t off; uint32_t cnt, pad; };
@@ -480,15 +484,17 @@ __global__ void __launch_bounds__(1024) k_scan_u32(const uint32_t* cnt, int P, u
 // the number of units starting at bucket b and uend[b] the end of a shared
 // unit.
 __global__ void k_count_units(const uint64_t* bstart, int P, int B2, uint64_t unit, int pack, uint32_t* K,
-                              uint64_t* uend) {
+                              uint64_t* uend, int light) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= P) return;
   const uint64_t s = bstart[b], len = bstart[b + 1] - s, W = unit / 2;
-  if (!pack || len > W) {
+  // sub-buckets light.. of every first-level bucket belong to single heavy keys
+  const bool own = light && (b & ((1 << B2) - 1)) >= light;
+  if (!pack || len > W || own) {
     K[b] = (uint32_t)((len + unit - 1) / unit);
     return;
   }
-  const int first = (b >> B2) << B2, last = first + (1 << B2);
+  const int first = (b >> B2) << B2, last = first + (light ? light : 1 << B2);
   const uint64_t base = bstart[first], g = (s - base) / W;
   const bool head = b == first || bstart[b] - bstart[b - 1] > W || (bstart[b - 1] - base) / W != g;
   if (!head) {
@@ -527,30 +533,140 @@ __global__ void k_emit_tiles(const uint64_t* bstart, int P, uint64_t tile_len, c
   tiles[t] = tl;
 }
 
+// ------------------------------------------------------------------ heavy bindings
+// A binding that holds a large share of the trace (a Zipf head) fills the
+// units of its sub-bucket almost alone; giving it a sub-bucket of its own
+// makes those units single-binding, folded without any grouping.  Heavy keys
+// are found from a sample of the trace (every HSTRIDE-th event); a miss or a
+// false hit changes only where a binding's records go, never the result.
+constexpr int HSTRIDE = 256;           // at least; more for traces over 2^27 events
+constexpr uint64_t HRECORDS = 8192;    // records that make a key heavy (about one unit)
+constexpr int HTAB_BITS = 20;          // largest sample table; it holds at most half as many samples
+constexpr int HMAXC = 64;              // heavy bindings per first-level bucket
+
+struct HeavyDev {
+  const uint32_t* cnt;                 // [P1] heavy bindings found per first-level bucket
+  const uint64_t* list;                // [P1][hmax] their record keys
+  int hmax;                            // 0: routing off
+};
+
+template <int F>
+__device__ __forceinline__ uint64_t mixed_key(uint64_t key) {
+  if (F == FMT_K32) return mix32((uint32_t)key);
+  return mix64(key);
+}
+
+// count sampled keys in a global open-addressing table (key 0: empty; a key
+// whose mix is 0 is never counted)
+template <int F>
+__global__ void k_hsample(const void* keyp, uint64_t n, uint64_t stride, int tbits, uint64_t* tk, uint32_t* tc) {
+  const uint64_t i = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) * stride;
+  const bool v = i < n;
+  const uint64_t m = v ? mixed_key<F>(load_key<F>(keyp, i)) : 0ull;
+  const bool want = v && m != 0;
+  const uint32_t peers = __match_any_sync(FULL, want ? m : 0ull);
+  if (!want || (int)(threadIdx.x & 31) != __ffs(peers) - 1) return;
+  uint32_t h = (uint32_t)((m * 0x9E3779B97F4A7C15ull) >> (64 - tbits));
+  for (int probe = 0; probe < (1 << tbits); ++probe) {
+    const unsigned long long prev = atomicCAS((unsigned long long*)&tk[h], 0ull, (unsigned long long)m);
+    if (prev == 0ull || prev == m) {
+      atomicAdd(&tc[h], (uint32_t)__popc(peers));
+      return;
+    }
+    h = (h + 1) & ((1u << tbits) - 1);
+  }
+}
+
+// keys sampled often enough become heavy: appended to their first-level
+// bucket's list as record keys (the mixed bits a record keeps)
+template <int F>
+__global__ void k_hpick(const uint64_t* tk, const uint32_t* tc, int tbits, uint32_t thresh, int B1, int hmax,
+                        uint32_t* hcnt, uint64_t* hlist) {
+  const uint32_t h = blockIdx.x * blockDim.x + threadIdx.x;
+  if (h >= (1u << tbits) || tc[h] < thresh) return;
+  const uint64_t m = tk[h];
+  const int W = F == FMT_K32 ? 32 : 64;
+  const uint32_t b1 = (uint32_t)(m >> (W - B1));
+  const uint64_t local = m & (W == 32 ? (0xFFFFFFFFull >> B1) : (~0ull >> B1));
+  const uint32_t j = atomicAdd(&hcnt[b1], 1u);
+  if (j < (uint32_t)hmax) hlist[(uint64_t)b1 * hmax + j] = local;
+}
+
+// the first-level bucket's heavy record keys, staged for broadcast reads
+__device__ __forceinline__ int load_heavy(const HeavyDev& hv, uint32_t b1, uint64_t* hl, int lane0, int step) {
+  if (!hv.hmax) return 0;
+  const int nh = (int)min(hv.cnt[b1], (uint32_t)hv.hmax);
+  for (int j = lane0; j < nh; j += step) hl[j] = hv.list[(uint64_t)b1 * hv.hmax + j];
+  return nh;
+}
+
+// A direct-mapped filter over the low 8 bits of a record key: j + 1 for the
+// heavy key j that has them, 0 for none, 0xFF when several share them.  Built
+// by one thread; nh <= HMAXC.
+__device__ __forceinline__ void build_filter(uint8_t* filt, const uint64_t* hl, int nh) {
+  for (int i = 0; i < 256; ++i) filt[i] = 0;
+  for (int j = 0; j < nh; ++j) {
+    const int h = (int)(hl[j] & 255u);
+    filt[h] = filt[h] ? 0xFF : (uint8_t)(j + 1);
+  }
+}
+
+// second-level sub-bucket of a record: its own for a heavy key (P2L + j),
+// else the next B2 bits of the mixed key
+__device__ __forceinline__ uint32_t sub_of(uint64_t rec, int sh, uint32_t P2L, const uint64_t* hl, const uint8_t* filt,
+                                           int nh) {
+  uint32_t sb = (uint32_t)(rec >> sh) & (P2L - 1);
+  if (nh == 0) return sb;
+  const uint64_t lk = rec >> 8;
+  const uint32_t f = filt[lk & 255u];
+  // branch-free for the common cases (no heavy key, one heavy key behind the filter entry)
+  const uint32_t j = (f - 1u) & (HMAXC - 1);
+  sb = (f - 1u < (uint32_t)nh && hl[j] == lk) ? P2L + j : sb;
+  if (f == 0xFF) {
+    for (int q = 0; q < nh; ++q)
+      if (hl[q] == lk) sb = P2L + q;
+  }
+  return sb;
+}
+
 // ------------------------------------------------------------------ level-2 multisplit
 template <int F>
-__global__ void __launch_bounds__(SC_WARPS * 32)
+__global__ void __launch_bounds__(SC_WARPS * 32, 6)
 k_hist2(const typename RecT<F>::type* recs, const Tile* tiles, const unsigned int* n_tiles, int B1, int B2,
-        uint32_t* hist2) {
-  __shared__ uint32_t cnt_all[SC_WARPS][128];
-  const int P2 = 1 << B2;
+        uint32_t* hist2, HeavyDev hv) {
+  __shared__ uint32_t cnt_all[SC_WARPS][256];
+  __shared__ uint64_t hl_all[SC_WARPS][HMAXC];
+  __shared__ uint8_t filt_all[SC_WARPS][256];
+  const uint32_t P2L = 1u << B2;
+  const int P2 = hv.hmax ? 2 << B2 : 1 << B2;    // light sub-buckets, then one per heavy key
   const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t tile = blockIdx.x * SC_WARPS + wl;
   if (tile >= *n_tiles) return;
   uint32_t* cnt = cnt_all[wl];
   for (int b = lane; b < P2; b += 32) cnt[b] = 0;
-  __syncwarp();
   const Tile tl = tiles[tile];
+  const int nh = load_heavy(hv, tl.bucket, hl_all[wl], lane, 32);
+  __syncwarp();
+  if (nh && lane == 0) build_filter(filt_all[wl], hl_all[wl], nh);
+  __syncwarp();
+  const uint64_t* hl = hl_all[wl];
+  const uint8_t* filt = filt_all[wl];
   const int sh = sub_shift<F>(B1, B2);
-  for (uint64_t base = tl.begin; base < tl.end; base += 32 * BATCH) {
-    uint32_t b[BATCH];
+  for (uint64_t base = tl.begin; base < tl.end; base += 32 * HBATCH) {
+    typename RecT<F>::type r[HBATCH];
+    uint32_t b[HBATCH];
 #pragma unroll
-    for (int j = 0; j < BATCH; ++j) {
+    for (int j = 0; j < HBATCH; ++j) {   // all loads first, so that they are in flight together
       const uint64_t i = base + j * 32 + lane;
-      b[j] = i < tl.end ? (uint32_t)((uint64_t)recs[i] >> sh) & (P2 - 1) : 0xFFFFFFFFu;
+      r[j] = i < tl.end ? recs[i] : 0;
     }
 #pragma unroll
-    for (int j = 0; j < BATCH; ++j)
+    for (int j = 0; j < HBATCH; ++j) {
+      const uint64_t i = base + j * 32 + lane;
+      b[j] = i < tl.end ? sub_of((uint64_t)r[j], sh, P2L, hl, filt, nh) : 0xFFFFFFFFu;
+    }
+#pragma unroll
+    for (int j = 0; j < HBATCH; ++j)
       if (b[j] != 0xFFFFFFFFu) atomicAdd(&cnt[b[j]], 1u);
   }
   __syncwarp();
@@ -558,62 +674,71 @@ k_hist2(const typename RecT<F>::type* recs, const Tile* tiles, const unsigned in
 }
 
 // per (first-level bucket, sub-bucket): exclusive prefix over the bucket's
-// tiles.  One CTA per first-level bucket: SCAN_ROWS rows of threads each take
-// a contiguous share of the tiles for every sub-bucket column, the rows' sums
-// are scanned in shared memory, then every row writes its share's prefixes.
-constexpr int SCAN_ROWS = 8;
-__global__ void __launch_bounds__(128 * SCAN_ROWS)
+// tiles.  One CTA per first-level bucket: rows of threads each take a
+// contiguous share of the tiles for every sub-bucket column (2^B2 columns),
+// the rows' sums are scanned in shared memory, then every row writes its
+// share's prefixes.
+__global__ void __launch_bounds__(1024)
 k_scan2(uint32_t* hist2, const uint32_t* tfirst, const uint32_t* tK, int P1, int B2, uint64_t* tot2) {
-  __shared__ uint64_t part[SCAN_ROWS][128];
-  const int P2 = 1 << B2;
+  __shared__ uint64_t part[1024];
+  const int P2 = 1 << B2, rows = 1024 >> B2;
   const int b1 = blockIdx.x;
-  const int col = threadIdx.x & 127, row = threadIdx.x >> 7;
+  const int col = threadIdx.x & (P2 - 1), row = threadIdx.x >> B2;
   const uint32_t f = tfirst[b1], k = tK[b1];
-  const uint32_t share = (k + SCAN_ROWS - 1) / SCAN_ROWS;
+  const uint32_t share = (k + rows - 1) / rows;
   const uint32_t j0 = min(k, row * share), j1 = min(k, j0 + share);
   uint64_t sum = 0;
-  if (col < P2)
-    for (uint32_t j = j0; j < j1; ++j) sum += hist2[(uint64_t)(f + j) * P2 + col];
-  part[row][col] = sum;
+  for (uint32_t j = j0; j < j1; ++j) sum += hist2[(uint64_t)(f + j) * P2 + col];
+  part[threadIdx.x] = sum;
   __syncthreads();
   uint64_t run = 0;
-  for (int r = 0; r < row; ++r) run += part[r][col];
-  if (col < P2) {
-    for (uint32_t j = j0; j < j1; ++j) {
-      const uint64_t idx = (uint64_t)(f + j) * P2 + col;
-      const uint32_t x = hist2[idx];
-      hist2[idx] = (uint32_t)run;
-      run += x;
-    }
-    if (row == SCAN_ROWS - 1) tot2[(b1 << B2) + col] = run;
+  for (int r = 0; r < row; ++r) run += part[(r << B2) + col];
+  for (uint32_t j = j0; j < j1; ++j) {
+    const uint64_t idx = (uint64_t)(f + j) * P2 + col;
+    const uint32_t x = hist2[idx];
+    hist2[idx] = (uint32_t)run;
+    run += x;
   }
+  if (row == rows - 1) tot2[((uint64_t)b1 << B2) + col] = run;
 }
 
 template <int F>
 __global__ void __launch_bounds__(SC_WARPS * 32)
 k_scatter2(const typename RecT<F>::type* in, const Tile* tiles, const unsigned int* n_tiles, int B1, int B2,
-           const uint32_t* pre2, const uint64_t* bstart2, typename RecT<F>::type* out) {
-  __shared__ uint32_t cur_all[SC_WARPS][128];
-  const int P2 = 1 << B2;
+           const uint32_t* pre2, const uint64_t* bstart2, typename RecT<F>::type* out, HeavyDev hv) {
+  __shared__ uint32_t cur_all[SC_WARPS][256];
+  __shared__ uint64_t hl_all[SC_WARPS][HMAXC];
+  __shared__ uint8_t filt_all[SC_WARPS][256];
+  const uint32_t P2L = 1u << B2;
+  const int B2e = hv.hmax ? B2 + 1 : B2;
+  const int P2 = 1 << B2e;
   const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t tile = blockIdx.x * SC_WARPS + wl;
   if (tile >= *n_tiles) return;
   const Tile tl = tiles[tile];
   uint32_t* cur = cur_all[wl];
   for (int b = lane; b < P2; b += 32)
-    cur[b] = (uint32_t)(bstart2[((uint64_t)tl.bucket << B2) + b] + pre2[(uint64_t)tile * P2 + b]);
+    cur[b] = (uint32_t)(bstart2[((uint64_t)tl.bucket << B2e) + b] + pre2[(uint64_t)tile * P2 + b]);
+  const int nh = load_heavy(hv, tl.bucket, hl_all[wl], lane, 32);
   __syncwarp();
+  if (nh && lane == 0) build_filter(filt_all[wl], hl_all[wl], nh);
+  __syncwarp();
+  const uint64_t* hl = hl_all[wl];
+  const uint8_t* filt = filt_all[wl];
   const int sh = sub_shift<F>(B1, B2);
   const uint32_t lt = lanemask_lt();
   for (uint64_t base = tl.begin; base < tl.end; base += 32 * BATCH) {
     typename RecT<F>::type rec[BATCH];
     uint32_t b[BATCH];
 #pragma unroll
+    for (int j = 0; j < BATCH; ++j) {   // all loads first, so that they are in flight together
+      const uint64_t i = base + j * 32 + lane;
+      rec[j] = i < tl.end ? in[i] : 0;
+    }
+#pragma unroll
     for (int j = 0; j < BATCH; ++j) {
       const uint64_t i = base + j * 32 + lane;
-      rec[j] = 0;
-      b[j] = 0xFFFFFFFFu;
-      if (i < tl.end) { rec[j] = in[i]; b[j] = (uint32_t)((uint64_t)rec[j] >> sh) & (P2 - 1); }
+      b[j] = i < tl.end ? sub_of((uint64_t)rec[j], sh, P2L, hl, filt, nh) : 0xFFFFFFFFu;
     }
 #pragma unroll
     for (int j = 0; j < BATCH; ++j) {
@@ -639,16 +764,18 @@ struct Tile2Shared {
   typename RecT<F>::type orec[Tile2Len<F>::v];
   uint32_t ibr[Tile2Len<F>::v];
   uint8_t ob[Tile2Len<F>::v];
-  uint32_t wcur[TB_WARPS][128];
-  uint32_t loc[128];
-  uint64_t gbase[128];
+  uint32_t wcur[TB_WARPS][256];
+  uint32_t loc[256];
+  uint64_t gbase[256];
+  uint64_t hl[HMAXC];
+  uint8_t filt[256];
   uint32_t tsum[TB_WARPS];
 };
 
 template <int F>
 __global__ void __launch_bounds__(TB_THREADS, 2)
 k_scatter2_tile(const typename RecT<F>::type* in, const Tile* tiles, const unsigned int* n_tiles, int B1, int B2,
-                const uint32_t* pre2, const uint64_t* bstart2, typename RecT<F>::type* out) {
+                const uint32_t* pre2, const uint64_t* bstart2, typename RecT<F>::type* out, HeavyDev hv) {
   typedef typename RecT<F>::type Rec;
   constexpr int T = Tile2Len<F>::v, R = T / TB_THREADS, PER = T / TB_WARPS;
   extern __shared__ __align__(16) unsigned char tile2_smem[];
@@ -657,10 +784,15 @@ k_scatter2_tile(const typename RecT<F>::type* in, const Tile* tiles, const unsig
   if (tile >= *n_tiles) return;
   const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t lt = lanemask_lt();
-  const int P2 = 1 << B2;
+  const uint32_t P2L = 1u << B2;
+  const int B2e = hv.hmax ? B2 + 1 : B2;
+  const int P2 = 1 << B2e;
   const Tile tl = tiles[tile];
   const int len = (int)(tl.end - tl.begin);      // <= T by construction
-  for (int i = threadIdx.x; i < TB_WARPS * 128; i += TB_THREADS) S.wcur[i / 128][i % 128] = 0;
+  for (int i = threadIdx.x; i < TB_WARPS * 256; i += TB_THREADS) S.wcur[i / 256][i % 256] = 0;
+  const int nh = load_heavy(hv, tl.bucket, S.hl, threadIdx.x, TB_THREADS);
+  __syncthreads();
+  if (nh && threadIdx.x == 0) build_filter(S.filt, S.hl, nh);
   __syncthreads();
   const int sh = sub_shift<F>(B1, B2);
   const int w0 = wl * PER;
@@ -675,14 +807,14 @@ k_scatter2_tile(const typename RecT<F>::type* in, const Tile* tiles, const unsig
   for (int j = 0; j < R; ++j) {
     const int i = w0 + j * 32 + lane;
     const bool v = i < len;
-    const uint32_t b = (uint32_t)((uint64_t)rec[j] >> sh) & (uint32_t)(P2 - 1);
+    const uint32_t b = sub_of((uint64_t)rec[j], sh, P2L, S.hl, S.filt, nh);
     const uint32_t rank = warp_rank(b, v, S.wcur[wl], lt);
     if (v) S.ibr[i] = b | (rank << 8);
   }
   __syncthreads();
-  tile_scan<128>(S.wcur, S.loc, S.tsum, P2);
+  tile_scan<256>(S.wcur, S.loc, S.tsum, P2);
   if ((int)threadIdx.x < P2)
-    S.gbase[threadIdx.x] = bstart2[((uint64_t)tl.bucket << B2) + threadIdx.x] + pre2[(uint64_t)tile * P2 + threadIdx.x];
+    S.gbase[threadIdx.x] = bstart2[((uint64_t)tl.bucket << B2e) + threadIdx.x] + pre2[(uint64_t)tile * P2 + threadIdx.x];
   __syncthreads();
 #pragma unroll
   for (int j = 0; j < R; ++j) {
@@ -730,6 +862,7 @@ __device__ __forceinline__ void inc6(uint32_t* h, uint32_t v) {
 struct Params {
   MonitorTab tab;
   int B1, B2, nq;
+  int light;           // heavy routing: sub-buckets light.. of a first-level bucket hold one binding each
   Acc* acc;
   rv_bindings out;
   int stream_mode;     // 1: fold the batch into StreamState instead of starting from q0
@@ -1204,6 +1337,7 @@ k_fold(const typename RecT<F>::type* recs, const Tile* units, const unsigned int
     bool ahead = false;                                             // next unit looked up yet
     const bool single = t.K == 1;
     const bool use_state = single && !p.stream_mode;   // a single unit starting at q0: plain states
+    const bool one_key = p.light && (int)(t.bucket & ((1u << p.B2) - 1)) >= p.light;
     const int len = (int)(t.end - t.begin);            // <= FoldCfg<F>::UNIT by construction
     if (threadIdx.x == 0) {
       S.npass = 1; S.pass_bits[0] = 0; S.pass_val[0] = 0;
@@ -1251,6 +1385,31 @@ k_fold(const typename RecT<F>::type* recs, const Tile* units, const unsigned int
           mbar_wait(&S.mbar, bulk_phase ^ 1u);
         }
         break;
+      }
+      if (one_key) {
+        // a heavy binding's own sub-bucket: fold the unit in place, in pieces
+        const int c = ((len + nthr - 1) / nthr) | 1;   // odd: conflict-free reads across the warp
+        const int a = min(len, (int)threadIdx.x * c), z = min(len, a + c);
+        uint64_t M = IDENTITY_MAP;
+        for (int i = a; i < z; ++i) {
+          const uint32_t l = BULK ? P[i] & 0xFFu : (uint32_t)((uint64_t)recs[t.begin + i] & 0xFFu);
+          M = apply_map(M, S.lmap[l], ns);
+        }
+        for (int off = 1; off < 32; off <<= 1) {
+          const uint64_t o = __shfl_down_sync(FULL, M, off);
+          if ((lane & (2 * off - 1)) == 0) M = apply_map(M, o, ns);
+        }
+        if (lane == 0) S.wmaps[wl] = M;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          uint64_t T = S.wmaps[0];
+          for (int w = 1; w < FOLD_WARPS; ++w) T = apply_map(T, S.wmaps[w], ns);
+          if (single) finalize_slot<F>(p, fc, outer_of(S), (uint64_t)cand, T, t.bucket);
+          else pool[S.item_off] = Pair{(uint64_t)cand, T};
+          S.item_cnt = 1;
+          S.npass = 0;
+        }
+        continue;
       }
       // 1. slot and rank of every record of this warp's slice
 #pragma unroll 1
@@ -1631,7 +1790,10 @@ __global__ void k_root(const Acc* acc, Params p, uint64_t n, rv_result* out) {
 // ------------------------------------------------------------------ host side
 struct Plan {
   int F, B1, B2, P1, P, G_w, nchunk;
-  bool tiled;
+  int B2e, hmax;       // heavy routing: B2e = B2 + 1 sub-bucket bits, up to hmax heavy keys per first-level bucket
+  int htbits;          // heavy routing: log2 of the sample table
+  uint64_t hstride;    // heavy routing: one sample every hstride events
+  bool tiled, heavy;
   uint64_t n, per_warp, unit, tile2;
   uint64_t max_tiles2, max_units;
   int levels;
@@ -1639,7 +1801,7 @@ struct Plan {
   // workspace offsets
   size_t o_acc, o_hist, o_part, o_tot1, o_bstart1, o_recA, o_recB, o_tiles2, o_tf2, o_tk2, o_hist2, o_tot2,
       o_bstart2, o_units, o_uf, o_uk, o_items0, o_items1, o_groups, o_gf0, o_gk0, o_gf1, o_gk1, o_pool0,
-      o_pool1, o_res, o_hkey, o_hpred, o_hts, o_uend, total;
+      o_pool1, o_res, o_hkey, o_hpred, o_hts, o_uend, o_htk, o_htc, o_hcnt, o_hlist, total;
 };
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -1654,7 +1816,8 @@ static int num_sms() {
   return sms;
 }
 
-static Plan make_plan(const rv_formula* f, uint64_t n, int host_input, const rv_verify_opts* o, int extra_b2) {
+static Plan make_plan(const rv_formula* f, uint64_t n, int host_input, const rv_verify_opts* o, int extra_b2,
+                      bool stream = false) {
   Plan pl{};
   pl.n = n;
   pl.F = f->n_quant == 2 ? FMT_K2 : (f->key_bits == 64 && f->n_quant == 1 ? FMT_K64 : FMT_K32);
@@ -1668,7 +1831,13 @@ static Plan make_plan(const rv_formula* f, uint64_t n, int host_input, const rv_
   else while (b2 < 7 && (n >> (pl.B1 + b2)) > 8192) ++b2;
   b2 += extra_b2;
   pl.B2 = std::min(7, std::max(0, b2));
-  pl.P = pl.P1 << pl.B2;
+  pl.heavy = pl.F != FMT_K2 && f->n_quant == 1 && pl.B2 > 0 && !stream && !(o && o->no_heavy);
+  pl.B2e = pl.B2 + (pl.heavy ? 1 : 0);
+  pl.hmax = pl.heavy ? std::min(HMAXC, 1 << pl.B2) : 0;
+  pl.hstride = std::max<uint64_t>(HSTRIDE, (n >> (HTAB_BITS - 1)) + 1);
+  pl.htbits = 10;
+  while (pl.htbits < HTAB_BITS && ((uint64_t)1 << (pl.htbits - 1)) < (n + pl.hstride - 1) / pl.hstride) ++pl.htbits;
+  pl.P = pl.P1 << pl.B2e;
   const uint64_t unit_max = pl.F == FMT_K32 ? FoldCfg<FMT_K32>::UNIT : FoldCfg<FMT_K64>::UNIT;
   pl.unit = o && o->unit_records ? (uint64_t)o->unit_records : unit_max;
   pl.unit = std::min<uint64_t>(unit_max, std::max<uint64_t>(256, pl.unit));
@@ -1704,13 +1873,17 @@ static Plan make_plan(const rv_formula* f, uint64_t n, int host_input, const rv_
   pl.o_tiles2 = pl.B2 ? take(pl.max_tiles2 * sizeof(Tile)) : 0;
   pl.o_tf2 = pl.B2 ? take((size_t)pl.P1 * 4) : 0;
   pl.o_tk2 = pl.B2 ? take((size_t)pl.P1 * 4) : 0;
-  pl.o_hist2 = pl.B2 ? take(pl.max_tiles2 * ((size_t)1 << pl.B2) * 4) : 0;
+  pl.o_hist2 = pl.B2 ? take(pl.max_tiles2 * ((size_t)1 << pl.B2e) * 4) : 0;
   pl.o_tot2 = pl.B2 ? take((size_t)pl.P * 8) : 0;
   pl.o_bstart2 = pl.B2 ? take((size_t)(pl.P + 1) * 8) : pl.o_bstart1;
   pl.o_units = take(pl.max_units * sizeof(Tile));
   pl.o_uf = take((size_t)pl.P * 4);
   pl.o_uk = take((size_t)pl.P * 4);
   pl.o_uend = take((size_t)pl.P * 8);
+  pl.o_htk = pl.heavy ? take(((size_t)1 << pl.htbits) * 8) : 0;
+  pl.o_htc = pl.heavy ? take(((size_t)1 << pl.htbits) * 4) : 0;
+  pl.o_hcnt = pl.heavy ? take((size_t)pl.P1 * 4) : 0;
+  pl.o_hlist = pl.heavy ? take((size_t)pl.P1 * pl.hmax * 8) : 0;
   pl.o_items0 = take(pl.max_units * sizeof(Item));
   pl.o_items1 = take(pl.max_units * sizeof(Item));
   pl.o_groups = take(pl.max_units * sizeof(Group));
@@ -1759,7 +1932,8 @@ static rv_status launch_all(const Plan& pl, const rv_formula* f, const void* key
   memset(&p, 0, sizeof p);
   p.tab = make_tab(f);
   p.B1 = pl.B1;
-  p.B2 = pl.B2;
+  p.B2 = pl.B2e;                       // sub-bucket bits of a bucket index
+  p.light = pl.heavy ? 1 << pl.B2 : 0;
   p.nq = f->n_quant;
   p.acc = acc;
   if (b) p.out = *b;
@@ -1802,15 +1976,31 @@ static rv_status launch_all(const Plan& pl, const rv_formula* f, const void* key
       RV_LAUNCH("k_scan_u32", k_scan_u32, 1, 1024, 0, s, tk2, pl.P1, tf2, &acc->n_tiles2);
       RV_LAUNCH("k_emit_tiles", k_emit_tiles, (int)((pl.max_tiles2 + 255) / 256), 256, 0, s, bstart1, pl.P1, pl.tile2, tf2, tk2, &acc->n_tiles2, tiles2);
       const int t2_blocks = (int)((pl.max_tiles2 + SC_WARPS - 1) / SC_WARPS);
-      RV_LAUNCH("k_hist2", k_hist2<F>, t2_blocks, SC_WARPS * 32, 0, s, recA, tiles2, &acc->n_tiles2, pl.B1, pl.B2, hist2);
-      RV_LAUNCH("k_scan2", k_scan2, pl.P1, 128 * SCAN_ROWS, 0, s, hist2, tf2, tk2, pl.P1, pl.B2, tot2);
+      HeavyDev hv{nullptr, nullptr, 0};
+      if (pl.heavy) {
+        uint64_t* htk = (uint64_t*)(ws + pl.o_htk);
+        uint32_t* htc = (uint32_t*)(ws + pl.o_htc);
+        uint32_t* hcnt = (uint32_t*)(ws + pl.o_hcnt);
+        uint64_t* hlist = (uint64_t*)(ws + pl.o_hlist);
+        RV_CU(cudaMemsetAsync(htk, 0, ((size_t)1 << pl.htbits) * 8, s));
+        RV_CU(cudaMemsetAsync(htc, 0, ((size_t)1 << pl.htbits) * 4, s));
+        RV_CU(cudaMemsetAsync(hcnt, 0, (size_t)pl.P1 * 4, s));
+        const uint64_t samples = (n + pl.hstride - 1) / pl.hstride;
+        const uint32_t thresh = (uint32_t)std::max<uint64_t>(8, HRECORDS / pl.hstride);
+        RV_LAUNCH("k_hsample", k_hsample<F>, (int)((samples + 255) / 256), 256, 0, s, key, n, pl.hstride, pl.htbits, htk, htc);
+        RV_LAUNCH("k_hpick", k_hpick<F>, (1 << pl.htbits) / 256, 256, 0, s, htk, htc, pl.htbits, thresh, pl.B1, pl.hmax, hcnt,
+                  hlist);
+        hv = HeavyDev{hcnt, hlist, pl.hmax};
+      }
+      RV_LAUNCH("k_hist2", k_hist2<F>, t2_blocks, SC_WARPS * 32, 0, s, recA, tiles2, &acc->n_tiles2, pl.B1, pl.B2, hist2, hv);
+      RV_LAUNCH("k_scan2", k_scan2, pl.P1, 1024, 0, s, hist2, tf2, tk2, pl.P1, pl.B2e, tot2);
       RV_LAUNCH("k_bucket_scan", k_bucket_scan, 1, 1024, 0, s, tot2, pl.P, bstart2);
       if (F == FMT_K32)
         RV_LAUNCH("k_scatter2", k_scatter2<F>, t2_blocks, SC_WARPS * 32, 0, s, recA, tiles2, &acc->n_tiles2, pl.B1, pl.B2, hist2,
-                  bstart2, recB);
+                  bstart2, recB, hv);
       else
         RV_LAUNCH("k_scatter2_tile", k_scatter2_tile<F>, (int)pl.max_tiles2, TB_THREADS, sizeof(Tile2Shared<F>), s, recA, tiles2,
-                  &acc->n_tiles2, pl.B1, pl.B2, hist2, bstart2, recB);
+                  &acc->n_tiles2, pl.B1, pl.B2, hist2, bstart2, recB, hv);
       recs = recB;
       bstart = bstart2;
     }
@@ -1823,7 +2013,8 @@ static rv_status launch_all(const Plan& pl, const rv_formula* f, const void* key
     Pair* pool0 = (Pair*)(ws + pl.o_pool0);
     Pair* pool1 = (Pair*)(ws + pl.o_pool1);
     uint64_t* uend = (uint64_t*)(ws + pl.o_uend);
-    RV_LAUNCH("k_count_units", k_count_units, (pl.P + 255) / 256, 256, 0, s, bstart, pl.P, pl.B2, pl.unit, F != FMT_K2 ? 1 : 0, uk, uend);
+    RV_LAUNCH("k_count_units", k_count_units, (pl.P + 255) / 256, 256, 0, s, bstart, pl.P, pl.B2e, pl.unit, F != FMT_K2 ? 1 : 0, uk, uend,
+              pl.heavy ? 1 << pl.B2 : 0);
     RV_LAUNCH("k_scan_u32", k_scan_u32, 1, 1024, 0, s, uk, pl.P, uf, &acc->n_units);
     RV_LAUNCH("k_emit_tiles", k_emit_tiles, (int)((pl.max_units + 255) / 256), 256, 0, s, bstart, pl.P, pl.unit, uf, uk, &acc->n_units, units,
               F != FMT_K2 ? uend : nullptr);
@@ -1909,7 +2100,7 @@ rv_status rv_offline_stream_batch(const rv_formula* f, const uint64_t* key, cons
                                   cudaStream_t s) {
   rv_formula g = *f;
   g.key_bits = 64;                       // ids are passed as 64-bit keys
-  Plan pl = make_plan(&g, n, 0, nullptr, 0);
+  Plan pl = make_plan(&g, n, 0, nullptr, 0, true);
   if (ws_bytes < pl.total) return rv_fail(RV_ENOMEM, "stream workspace of %zu bytes, need %zu", ws_bytes, pl.total);
   rv_status st = dispatch(pl, &g, key, pred, nullptr, (unsigned char*)ws, nullptr, nullptr, s, ss);
   if (st) return st;
@@ -1921,7 +2112,7 @@ rv_status rv_offline_stream_batch(const rv_formula* f, const uint64_t* key, cons
 size_t rv_offline_stream_ws(const rv_formula* f, uint64_t n) {
   rv_formula g = *f;
   g.key_bits = 64;
-  return make_plan(&g, n, 0, nullptr, 0).total;
+  return make_plan(&g, n, 0, nullptr, 0, true).total;
 }
 
 extern "C" void rv_set_allocator(rv_alloc_fn alloc, rv_free_fn free_fn, void* ctx) {

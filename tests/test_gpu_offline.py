@@ -238,3 +238,12 @@ def test_units_that_open_with_one_binding(rv, torch_cuda):
     opts = {"bucket_bits": 8, "sub_bucket_bits": 7, "unit_records": 256}
     for body in ["G(receive -> F respond)", "F(receive && X respond)", "(receive U respond) || F socket"]:
         _check(rv, torch_cuda, f"A_{{>=0.5}} x: p(x) => {body}", synth.SOCKET_CODES, key, pred, opts=opts)
+
+
+@pytest.mark.parametrize("opts", [{"sub_bucket_bits": 3}, {"sub_bucket_bits": 3, "no_heavy": 1},
+                                  {"sub_bucket_bits": 2, "unit_records": 1024}])
+def test_zipf_heads_in_own_sub_buckets(rv, torch_cuda, opts):
+    # Zipf(1.1) over 2e4 ids: the head keys are found by sampling and folded
+    # in sub-buckets of their own (or not, with no_heavy); both must match
+    tr = synth.socket_trace(3_000_000, 20_000, pending_frac=0.03, zipf_s=1.1, seed=31)
+    _check(rv, torch_cuda, C1, tr.codes, tr.key, tr.pred, opts=opts)
