@@ -341,50 +341,6 @@ __global__ void k_colscan_c(uint32_t* hist, int G_w, int P, int nchunk, const ui
   }
 }
 
-// single CTA: exclusive scan of tot[0..P) into bstart[0..P].  Thread t owns
-// a contiguous chunk; its loads go out eight at a time.
-__global__ void __launch_bounds__(1024) k_bucket_scan(const uint64_t* tot, int P, uint64_t* bstart) {
-  __shared__ uint64_t wsum[32];
-  const int t = threadIdx.x;
-  const int per = (P + 1023) / 1024;
-  const int b0 = min(P, t * per), b1 = min(P, b0 + per);
-  uint64_t s = 0;
-  for (int b = b0; b < b1; b += 8) {
-    uint64_t v[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) v[j] = b + j < b1 ? tot[b + j] : 0ull;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) s += v[j];
-  }
-  // block exclusive scan of s
-  uint64_t x = s;
-  const int lane = t & 31, w = t >> 5;
-  for (int o = 1; o < 32; o <<= 1) {
-    uint64_t y = __shfl_up_sync(FULL, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) wsum[w] = x;
-  __syncthreads();
-  if (w == 0) {
-    uint64_t z = wsum[lane];
-    for (int o = 1; o < 32; o <<= 1) {
-      uint64_t y = __shfl_up_sync(FULL, z, o);
-      if (lane >= o) z += y;
-    }
-    wsum[lane] = z;
-  }
-  __syncthreads();
-  uint64_t run = x - s + (w ? wsum[w - 1] : 0);
-  for (int b = b0; b < b1; b += 8) {
-    uint64_t v[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) v[j] = b + j < b1 ? tot[b + j] : 0ull;
-#pragma unroll
-    for (int j = 0; j < 8; ++j)
-      if (b + j < b1) { bstart[b + j] = run; run += v[j]; }
-  }
-  if (t == 1023) bstart[P] = run;
-}
 
 template <int F>
 __global__ void __launch_bounds__(SC_WARPS * 32)
@@ -443,61 +399,65 @@ __global__ void k_count_tiles(const uint64_t* bstart, int P, uint64_t tile_len, 
   K[b] = (uint32_t)((len + tile_len - 1) / tile_len);
 }
 
-// single CTA: exclusive scan of cnt[0..P) into first[], total into *n.
-// Chunks of SCAN_CHUNK entries are staged in shared memory with coalesced
-// loads (padded by one word per 32, so that a thread's contiguous run of 32
-// entries falls into 32 banks), each thread scans its run, and the results go
-// back out coalesced.
-constexpr int SCAN_CHUNK = 32768;
-constexpr size_t SCAN_SMEM = (SCAN_CHUNK + SCAN_CHUNK / 32) * 4;
-__global__ void __launch_bounds__(1024) k_scan_u32(const uint32_t* cnt, int P, uint32_t* first, unsigned int* n) {
-  extern __shared__ uint32_t sc[];
-  __shared__ uint32_t wsum[32];
+// single CTA: exclusive scan of in[0..P) into out[0..P), total into *total.
+// Chunks are staged in shared memory with coalesced loads (padded by one word
+// per 32 entries, so that a thread's contiguous run of 32 entries falls into
+// 32 banks), each thread scans its run, and the results go back coalesced.
+template <typename T> struct ScanChunk { static constexpr int v = 32768; };
+template <> struct ScanChunk<uint64_t> { static constexpr int v = 16384; };
+template <typename T> constexpr size_t scan_smem() { return (ScanChunk<T>::v + ScanChunk<T>::v / 32) * sizeof(T); }
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_scan(const T* in, int P, T* out, T* total) {
+  constexpr int CH = ScanChunk<T>::v, RUN = CH / 1024;
+  extern __shared__ __align__(16) unsigned char scan_smem_raw[];
+  T* sc = reinterpret_cast<T*>(scan_smem_raw);
+  __shared__ T wsum[32];
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-  uint32_t carry = 0;
-  for (int base = 0; base < P; base += SCAN_CHUNK) {
-    const int len = min(SCAN_CHUNK, P - base);
-    for (int i = t; i < len; i += 1024) sc[i + (i >> 5)] = cnt[base + i];
+  T carry = 0;
+  for (int base = 0; base < P; base += CH) {
+    const int len = min(CH, P - base);
+    for (int i = t; i < len; i += 1024) sc[i + (i >> 5)] = in[base + i];
     __syncthreads();
-    const int i0 = t * 32;                       // this thread's run: entries i0 .. i0 + 31
-    uint32_t s = 0;
+    const int i0 = t * RUN;                      // this thread's run: entries i0 .. i0 + RUN - 1
+    T s = 0;
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
+    for (int j = 0; j < RUN; ++j) {
       const int i = i0 + j;
-      s += i < len ? sc[i + (i >> 5)] : 0u;
+      s += i < len ? sc[i + (i >> 5)] : (T)0;
     }
-    uint32_t x = s;
+    T x = s;
     for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(FULL, x, o);
+      const T y = __shfl_up_sync(FULL, x, o);
       if (lane >= o) x += y;
     }
     if (lane == 31) wsum[w] = x;
     __syncthreads();
     if (w == 0) {
-      uint32_t z = wsum[lane];
+      T z = wsum[lane];
       for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(FULL, z, o);
+        const T y = __shfl_up_sync(FULL, z, o);
         if (lane >= o) z += y;
       }
       wsum[lane] = z;
     }
     __syncthreads();
-    uint32_t run = carry + x - s + (w ? wsum[w - 1] : 0u);
+    T run = carry + x - s + (w ? wsum[w - 1] : (T)0);
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
+    for (int j = 0; j < RUN; ++j) {
       const int i = i0 + j;
       if (i < len) {
-        const uint32_t v = sc[i + (i >> 5)];
+        const T v = sc[i + (i >> 5)];
         sc[i + (i >> 5)] = run;
         run += v;
       }
     }
     carry += wsum[31];
     __syncthreads();
-    for (int i = t; i < len; i += 1024) first[base + i] = sc[i + (i >> 5)];
+    for (int i = t; i < len; i += 1024) out[base + i] = sc[i + (i >> 5)];
     __syncthreads();
   }
-  if (t == 0) *n = carry;
+  if (t == 0) *total = carry;
 }
 
 // Units of the fold.  A bucket longer than half a unit is cut into
@@ -1978,7 +1938,7 @@ static rv_status launch_all(const Plan& pl, const rv_formula* f, const void* key
     RV_LAUNCH("k_colscan_a", k_colscan_a, (ct + 255) / 256, 256, 0, s, hist, pl.G_w, pl.P1, pl.nchunk, part);
     RV_LAUNCH("k_colscan_b", k_colscan_b, (pl.P1 + 255) / 256, 256, 0, s, part, pl.P1, pl.nchunk, tot1);
     RV_LAUNCH("k_colscan_c", k_colscan_c, (ct + 255) / 256, 256, 0, s, hist, pl.G_w, pl.P1, pl.nchunk, part);
-    RV_LAUNCH("k_bucket_scan", k_bucket_scan, 1, 1024, 0, s, tot1, pl.P1, bstart1);
+    RV_LAUNCH("k_bucket_scan", k_scan<uint64_t>, 1, 1024, scan_smem<uint64_t>(), s, tot1, pl.P1, bstart1, bstart1 + pl.P1);
     if (pl.tiled)
       RV_LAUNCH("k_scatter_tile", k_scatter_tile<F>, pl.G_w, TB_THREADS, sizeof(TileShared<F>), s, key, pred, n,
                 f->n_quant, f->n_letters, hist, bstart1, recA, acc);
@@ -1996,7 +1956,7 @@ static rv_status launch_all(const Plan& pl, const rv_formula* f, const void* key
       uint64_t* bstart2 = (uint64_t*)(ws + pl.o_bstart2);
       Rec* recB = (Rec*)(ws + pl.o_recB);
       RV_LAUNCH("k_count_tiles", k_count_tiles, (pl.P1 + 255) / 256, 256, 0, s, bstart1, pl.P1, pl.tile2, tk2);
-      RV_LAUNCH("k_scan_u32", k_scan_u32, 1, 1024, SCAN_SMEM, s, tk2, pl.P1, tf2, &acc->n_tiles2);
+      RV_LAUNCH("k_scan_u32", k_scan<uint32_t>, 1, 1024, scan_smem<uint32_t>(), s, tk2, pl.P1, tf2, &acc->n_tiles2);
       RV_LAUNCH("k_emit_tiles", k_emit_tiles, (int)((pl.max_tiles2 + 255) / 256), 256, 0, s, bstart1, pl.P1, pl.tile2, tf2, tk2, &acc->n_tiles2, tiles2);
       const int t2_blocks = (int)((pl.max_tiles2 + SC_WARPS - 1) / SC_WARPS);
       HeavyDev hv{nullptr, nullptr, 0};
@@ -2017,7 +1977,7 @@ static rv_status launch_all(const Plan& pl, const rv_formula* f, const void* key
       }
       RV_LAUNCH("k_hist2", k_hist2<F>, t2_blocks, SC_WARPS * 32, 0, s, recA, tiles2, &acc->n_tiles2, pl.B1, pl.B2, hist2, hv);
       RV_LAUNCH("k_scan2", k_scan2, pl.P1, 1024, 0, s, hist2, tf2, tk2, pl.P1, pl.B2e, tot2);
-      RV_LAUNCH("k_bucket_scan", k_bucket_scan, 1, 1024, 0, s, tot2, pl.P, bstart2);
+      RV_LAUNCH("k_bucket_scan", k_scan<uint64_t>, 1, 1024, scan_smem<uint64_t>(), s, tot2, pl.P, bstart2, bstart2 + pl.P);
       if (F == FMT_K32)
         RV_LAUNCH("k_scatter2", k_scatter2<F>, t2_blocks, SC_WARPS * 32, 0, s, recA, tiles2, &acc->n_tiles2, pl.B1, pl.B2, hist2,
                   bstart2, recB, hv);
@@ -2038,7 +1998,7 @@ static rv_status launch_all(const Plan& pl, const rv_formula* f, const void* key
     uint64_t* uend = (uint64_t*)(ws + pl.o_uend);
     RV_LAUNCH("k_count_units", k_count_units, (pl.P + 255) / 256, 256, 0, s, bstart, pl.P, pl.B2e, pl.unit, F != FMT_K2 ? 1 : 0, uk, uend,
               pl.heavy ? 1 << pl.B2 : 0);
-    RV_LAUNCH("k_scan_u32", k_scan_u32, 1, 1024, SCAN_SMEM, s, uk, pl.P, uf, &acc->n_units);
+    RV_LAUNCH("k_scan_u32", k_scan<uint32_t>, 1, 1024, scan_smem<uint32_t>(), s, uk, pl.P, uf, &acc->n_units);
     RV_LAUNCH("k_emit_tiles", k_emit_tiles, (int)((pl.max_units + 255) / 256), 256, 0, s, bstart, pl.P, pl.unit, uf, uk, &acc->n_units, units,
               F != FMT_K2 ? uend : nullptr);
     const int grid = (int)std::min<uint64_t>(pl.max_units, (uint64_t)num_sms() * FoldCfg<F>::MINB);
@@ -2055,7 +2015,7 @@ static rv_status launch_all(const Plan& pl, const rv_formula* f, const void* key
       const int dst = (l + 1) & 1;
       RV_CU(cudaMemsetAsync(&acc->pair_top[dst], 0, sizeof(unsigned long long), s));
       RV_LAUNCH("k_count_groups", k_count_groups, (pl.P + 255) / 256, 256, 0, s, kin, pl.P, gk[l & 1]);
-      RV_LAUNCH("k_scan_u32", k_scan_u32, 1, 1024, SCAN_SMEM, s, gk[l & 1], pl.P, gf[l & 1], &acc->n_groups[l]);
+      RV_LAUNCH("k_scan_u32", k_scan<uint32_t>, 1, 1024, scan_smem<uint32_t>(), s, gk[l & 1], pl.P, gf[l & 1], &acc->n_groups[l]);
       RV_LAUNCH("k_emit_groups", k_emit_groups, (pl.P + 255) / 256, 256, 0, s, fin, kin, pl.P, gf[l & 1], gk[l & 1], groups);
       const int cgrid = (int)std::min<uint64_t>(pl.max_units / GC + pl.P, (uint64_t)num_sms() * 2);
       RV_LAUNCH("k_combine", k_combine<F>, cgrid, FOLD_THREADS, sizeof(CombineShared), s, iin, pin, groups, &acc->n_groups[l], &acc->next_group[l], p,
@@ -2081,7 +2041,8 @@ static rv_status set_attrs() {
   RV_CU(cudaFuncSetAttribute(k_hist<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, SC_WARPS * 2048 * 4));
   RV_CU(cudaFuncSetAttribute(k_scatter<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, SC_WARPS * 2048 * 4));
   RV_CU(cudaFuncSetAttribute(k_scatter_tile<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TileShared<F>)));
-  RV_CU(cudaFuncSetAttribute(k_scan_u32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SCAN_SMEM));
+  RV_CU(cudaFuncSetAttribute(k_scan<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)scan_smem<uint32_t>()));
+  RV_CU(cudaFuncSetAttribute(k_scan<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)scan_smem<uint64_t>()));
   RV_CU(cudaFuncSetAttribute(k_scatter2_tile<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Tile2Shared<F>)));
   g_attr_done[F] = true;
   return RV_OK;
