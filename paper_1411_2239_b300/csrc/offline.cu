@@ -408,8 +408,9 @@ template <> struct ScanChunk<uint64_t> { static constexpr int v = 16384; };
 template <typename T> constexpr size_t scan_smem() { return (ScanChunk<T>::v + ScanChunk<T>::v / 32) * sizeof(T); }
 
 template <typename T>
-__global__ void __launch_bounds__(1024) k_scan(const T* in, int P, T* out, T* total) {
+__global__ void __launch_bounds__(1024) k_scan(const T* in, int P, T* out, T* total, const unsigned int* Pdev = nullptr) {
   constexpr int CH = ScanChunk<T>::v, RUN = CH / 1024;
+  if (Pdev) P = min(P, (int)*Pdev);
   extern __shared__ __align__(16) unsigned char scan_smem_raw[];
   T* sc = reinterpret_cast<T*>(scan_smem_raw);
   __shared__ T wsum[32];
@@ -1635,25 +1636,38 @@ k_fold(const typename RecT<F>::type* recs, const Tile* units, const unsigned int
 
 // Groups of up to GC consecutive items of every bucket still holding K >= 2
 // items; a bucket that ends up with one group is finalised by it.
-__global__ void k_count_groups(const uint32_t* K_in, int P, uint32_t* K_out) {
+// The buckets that more than one unit folds, listed once after k_fold (in
+// any order) with their unit counts and first units; the combine levels work
+// on this short list instead of on every bucket.
+__global__ void k_list_multi(const uint32_t* K, const uint32_t* first, int P, unsigned int* m, uint32_t* ids,
+                             uint32_t* K0, uint32_t* F0) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= P) return;
-  const uint32_t k = K_in[b];
-  K_out[b] = k >= 2 ? (k + GC - 1) / GC : 0u;
+  if (b >= P || K[b] < 2) return;
+  const unsigned int i = atomicAdd(m, 1u);
+  ids[i] = (uint32_t)b;
+  K0[i] = K[b];
+  F0[i] = first[b];
 }
 
-__global__ void k_emit_groups(const uint32_t* first_in, const uint32_t* K_in, int P, const uint32_t* first_out,
-                              const uint32_t* K_out, Group* groups) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= P) return;
-  const uint32_t k = K_in[b], g = K_out[b];
+__global__ void k_count_groups(const uint32_t* K_in, const unsigned int* m, uint32_t* K_out) {
+  const unsigned int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= *m) return;
+  const uint32_t k = K_in[i];
+  K_out[i] = k >= 2 ? (k + GC - 1) / GC : 0u;
+}
+
+__global__ void k_emit_groups(const uint32_t* first_in, const uint32_t* K_in, const unsigned int* m,
+                              const uint32_t* first_out, const uint32_t* K_out, const uint32_t* ids, Group* groups) {
+  const unsigned int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= *m) return;
+  const uint32_t k = K_in[i], g = K_out[i];
   for (uint32_t j = 0; j < g; ++j) {
     Group G;
-    G.bucket = (uint32_t)b;
-    G.first = first_in[b] + j * GC;
+    G.bucket = ids[i];
+    G.first = first_in[i] + j * GC;
     G.cnt = min((uint32_t)GC, k - j * GC);
     G.k = j; G.K = g; G.pad = 0;
-    groups[first_out[b] + j] = G;
+    groups[first_out[i] + j] = G;
   }
 }
 
@@ -1784,7 +1798,7 @@ struct Plan {
   // workspace offsets
   size_t o_acc, o_hist, o_part, o_tot1, o_bstart1, o_recA, o_recB, o_tiles2, o_tf2, o_tk2, o_hist2, o_tot2,
       o_bstart2, o_units, o_uf, o_uk, o_items0, o_items1, o_groups, o_gf0, o_gk0, o_gf1, o_gk1, o_pool0,
-      o_pool1, o_res, o_hkey, o_hpred, o_hts, o_uend, o_htk, o_htc, o_hcnt, o_hlist, total;
+      o_pool1, o_res, o_hkey, o_hpred, o_hts, o_uend, o_htk, o_htc, o_hcnt, o_hlist, o_mids, o_mk, o_mf, total;
 };
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -1863,6 +1877,9 @@ static Plan make_plan(const rv_formula* f, uint64_t n, int host_input, const rv_
   pl.o_uf = take((size_t)pl.P * 4);
   pl.o_uk = take((size_t)pl.P * 4);
   pl.o_uend = take((size_t)pl.P * 8);
+  pl.o_mids = take((size_t)pl.P * 4);
+  pl.o_mk = take((size_t)pl.P * 4);
+  pl.o_mf = take((size_t)pl.P * 4);
   pl.o_htk = pl.heavy ? take(((size_t)1 << pl.htbits) * 8) : 0;
   pl.o_htc = pl.heavy ? take(((size_t)1 << pl.htbits) * 4) : 0;
   pl.o_hcnt = pl.heavy ? take((size_t)pl.P1 * 4) : 0;
@@ -2003,8 +2020,12 @@ static rv_status launch_all(const Plan& pl, const rv_formula* f, const void* key
               F != FMT_K2 ? uend : nullptr);
     const int grid = (int)std::min<uint64_t>(pl.max_units, (uint64_t)num_sms() * FoldCfg<F>::MINB);
     RV_LAUNCH("k_fold", k_fold<F>, grid, FOLD_THREADS, sizeof(FoldShared<F>), s, recs, units, &acc->n_units, p, items0, pool0);
-    const uint32_t* fin = uf;
-    const uint32_t* kin = uk;
+    uint32_t* mids = (uint32_t*)(ws + pl.o_mids);
+    uint32_t* mk = (uint32_t*)(ws + pl.o_mk);
+    uint32_t* mf = (uint32_t*)(ws + pl.o_mf);
+    RV_LAUNCH("k_list_multi", k_list_multi, (pl.P + 255) / 256, 256, 0, s, uk, uf, pl.P, &acc->n_multi, mids, mk, mf);
+    const uint32_t* fin = mf;
+    const uint32_t* kin = mk;
     uint32_t* gf[2] = {(uint32_t*)(ws + pl.o_gf0), (uint32_t*)(ws + pl.o_gf1)};
     uint32_t* gk[2] = {(uint32_t*)(ws + pl.o_gk0), (uint32_t*)(ws + pl.o_gk1)};
     Item* iin = items0;
@@ -2014,9 +2035,11 @@ static rv_status launch_all(const Plan& pl, const rv_formula* f, const void* key
     for (int l = 0; l < pl.levels; ++l) {
       const int dst = (l + 1) & 1;
       RV_CU(cudaMemsetAsync(&acc->pair_top[dst], 0, sizeof(unsigned long long), s));
-      RV_LAUNCH("k_count_groups", k_count_groups, (pl.P + 255) / 256, 256, 0, s, kin, pl.P, gk[l & 1]);
-      RV_LAUNCH("k_scan_u32", k_scan<uint32_t>, 1, 1024, scan_smem<uint32_t>(), s, gk[l & 1], pl.P, gf[l & 1], &acc->n_groups[l]);
-      RV_LAUNCH("k_emit_groups", k_emit_groups, (pl.P + 255) / 256, 256, 0, s, fin, kin, pl.P, gf[l & 1], gk[l & 1], groups);
+      RV_LAUNCH("k_count_groups", k_count_groups, (pl.P + 255) / 256, 256, 0, s, kin, &acc->n_multi, gk[l & 1]);
+      RV_LAUNCH("k_scan_u32", k_scan<uint32_t>, 1, 1024, scan_smem<uint32_t>(), s, gk[l & 1], pl.P, gf[l & 1], &acc->n_groups[l],
+                &acc->n_multi);
+      RV_LAUNCH("k_emit_groups", k_emit_groups, (pl.P + 255) / 256, 256, 0, s, fin, kin, &acc->n_multi, gf[l & 1], gk[l & 1], mids,
+                groups);
       const int cgrid = (int)std::min<uint64_t>(pl.max_units / GC + pl.P, (uint64_t)num_sms() * 2);
       RV_LAUNCH("k_combine", k_combine<F>, cgrid, FOLD_THREADS, sizeof(CombineShared), s, iin, pin, groups, &acc->n_groups[l], &acc->next_group[l], p,
                                                                       iout, pout, dst);

@@ -189,6 +189,7 @@ struct Acc {
   unsigned long long pair_top[2];
   unsigned int next_unit;       // dynamic work distribution of k_fold
   unsigned int next_group[8];   // and of each k_combine level
+  unsigned int n_multi;         // buckets folded by more than one unit
 };
 
 // ------------------------------------------------------------------ streaming state
