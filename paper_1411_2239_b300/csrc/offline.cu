@@ -1101,6 +1101,7 @@ struct FoldShared {
   // bulk copy (16-byte aligned, so up to 4 extra records at either end)
   uint32_t pk[UNIT + 8];
   uint8_t sorted[UNIT];                // letters grouped by slot, trace order kept
+  uint8_t vslot[SL];                   // verdict of every slot (two quantifiers: counted after the pass)
   uint64_t tkey[HT];
   uint16_t tslot[PACKED ? 2 : HT];     // slot of tkey[h] (64-bit keys)
   uint64_t skey[SL];                   // key of every slot
@@ -1267,6 +1268,25 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   }
 }
 
+// A binding that a single unit holds whole: tallied now; for two quantifiers
+// its verdict is counted under its outer binding after the pass, with equal
+// (outer, verdict) pairs of a warp added at once.
+template <int F>
+__device__ __forceinline__ void fold_finalize(const Params& p, FinalCtx& fc, FoldShared<F>& S, int s, uint64_t skey,
+                                              uint64_t M, uint32_t bucket) {
+  if constexpr (F == FMT_K2) {
+    if (!p.stream_mode) {
+      const uint32_t v = p.tab.labels[(uint32_t)((M >> (4 * p.tab.q0)) & 15ull)];
+      inc6(fc.h1, v);
+      fc.nodes1 += 1;
+      S.vslot[s] = (uint8_t)v;
+      if (p.out.keys) emit_binding<F>(p, skey, bucket >> p.B2, v);
+      return;
+    }
+  }
+  finalize_slot<F>(p, fc, outer_of(S), skey, M, bucket);
+}
+
 // Fold of one unit (a contiguous range of one bucket's records):
 // (1) every warp takes a contiguous slice and gives each record its slot and
 //     its rank among the slot's records of the slice (ballot match per round);
@@ -1388,7 +1408,7 @@ k_fold(const typename RecT<F>::type* recs, const Tile* units, const unsigned int
         if (threadIdx.x == 0) {
           uint64_t T = S.wmaps[0];
           for (int w = 1; w < FOLD_WARPS; ++w) T = apply_map(T, S.wmaps[w], ns);
-          if (single) finalize_slot<F>(p, fc, outer_of(S), (uint64_t)cand, T, t.bucket);
+          if (single) fold_finalize<F>(p, fc, S, 0, (uint64_t)cand, T, t.bucket);
           else pool[S.item_off] = Pair{(uint64_t)cand, T};
           S.item_cnt = 1;
           S.npass = 0;
@@ -1535,7 +1555,7 @@ k_fold(const typename RecT<F>::type* recs, const Tile* units, const unsigned int
               for (uint32_t j = pos; j < end; ++j) V = apply_map(V, S.lmap[S.sorted[j]], ns);
             }
             if (starts && ends) {
-              if (single) finalize_slot<F>(p, fc, outer_of(S), S.skey[sl], V, t.bucket);
+              if (single) fold_finalize<F>(p, fc, S, sl, S.skey[sl], V, t.bucket);
               else pool[S.item_off + S.item_cnt + sl] = Pair{S.skey[sl], V};
             } else if (!starts) {
               S.firstmap[threadIdx.x] = V;          // continues a run begun in an earlier piece
@@ -1581,7 +1601,7 @@ k_fold(const typename RecT<F>::type* recs, const Tile* units, const unsigned int
               V = apply_map(V, Mq, ns);
             }
           }
-          if (single) finalize_slot<F>(p, fc, outer_of(S), S.skey[sl], V, t.bucket);
+          if (single) fold_finalize<F>(p, fc, S, sl, S.skey[sl], V, t.bucket);
           else pool[S.item_off + S.item_cnt + sl] = Pair{S.skey[sl], V};
         }
       }
@@ -1604,8 +1624,25 @@ k_fold(const typename RecT<F>::type* recs, const Tile* units, const unsigned int
         if (threadIdx.x == 0) {
           uint64_t T = S.wmaps[0];
           for (int w = 1; w < FOLD_WARPS; ++w) T = apply_map(T, S.wmaps[w], ns);
-          if (single) finalize_slot<F>(p, fc, outer_of(S), S.skey[0], T, t.bucket);
+          if (single) fold_finalize<F>(p, fc, S, 0, S.skey[0], T, t.bucket);
           else pool[S.item_off + S.item_cnt + 0] = Pair{S.skey[0], T};
+        }
+      }
+      if constexpr (F == FMT_K2) {
+        if (single && !p.stream_mode) {
+          __syncthreads();                   // every binding of this pass has its verdict
+          for (int base = 0; base < nsl; base += nthr) {
+            const int s = base + (int)threadIdx.x;
+            uint32_t code = 0xFFFFFFFFu;
+            if (s < nsl) {
+              const int ui = outer_slot(S.U, (uint32_t)(S.skey[s] >> 32));
+              if (ui < 0) atomicOr(&p.acc->err, ERR_OUTER_FULL);
+              else code = ((uint32_t)ui << 3) | S.vslot[s];
+            }
+            const uint32_t peers = __match_any_sync(FULL, code);
+            if (code != 0xFFFFFFFFu && lane == __ffs(peers) - 1)
+              atomicAdd(&S.U.ucnt[code >> 3][code & 7u], (uint32_t)__popc(peers));
+          }
         }
       }
       // clear the table entries and counters this pass used
