@@ -130,3 +130,34 @@ def test_valuation_large_counts_exact(rv):
         v = [0, 0, N - tp, tp, 0, 0]
         q = Quantifier("A", ">=", Fraction(num, den), "x", "p")
         assert rv.valuate(rv.Q_A, rv.OPS[">="], num, den, v) == counting.valuate(q, v)
+
+
+def _header_structs():
+    """Field names, in order, of every `typedef struct { ... } name;` in rv.h."""
+    import re
+    text = open(os.path.join(os.path.dirname(__file__), "..", "include", "rv.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    out = {}
+    for body, name in re.findall(r"typedef struct\s*\{(.*?)\}\s*(\w+)\s*;", text, flags=re.S):
+        fields = []
+        for decl in body.split(";"):
+            decl = decl.strip()
+            if not decl:
+                continue
+            first, *rest = decl.split(",")          # `uint64_t a, b, c;` declares three fields
+            for d in [first] + rest:
+                fields.append(re.findall(r"(\w+)\s*(?:\[[^\]]*\])*\s*$", d.strip())[0])
+        out[name] = fields
+    return out
+
+
+def test_binding_structs_mirror_the_header():
+    # the ctypes mirrors of the C structs keep the header's fields and order
+    from paper_1411_2239_b300 import rv
+    hs = _header_structs()
+    pairs = {"rv_schema": rv._Schema, "rv_formula_info": rv._Info, "rv_trace": rv._Trace, "rv_result": rv._Result,
+             "rv_bindings": rv._Bindings, "rv_verify_opts": rv._Opts, "rv_batch_opts": rv._BatchOpts,
+             "rv_service_cfg": rv._SvcCfg, "rv_stream_verdict": rv._Verdict, "rv_service_counters": rv._SvcCounters}
+    for cname, cls in pairs.items():
+        assert cname in hs, cname
+        assert [f[0] for f in cls._fields_] == hs[cname], (cname, hs[cname])
