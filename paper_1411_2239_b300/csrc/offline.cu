@@ -305,27 +305,52 @@ __device__ __forceinline__ void tile_scan(uint32_t (*wcur)[NB], uint32_t* loc, u
   }
 }
 
+// Sums and exclusive prefixes down a column p[0], p[s], p[2s], ...: the loads
+// of COLB entries are issued before any of their stores, so a thread waits
+// for one memory round trip per COLB entries rather than per entry.
+constexpr int COLB = 16;
+template <typename T>
+__device__ __forceinline__ uint64_t col_sum(const T* p, uint64_t s, uint32_t n) {
+  uint64_t sum = 0;
+  for (uint32_t j0 = 0; j0 < n; j0 += COLB) {
+    T x[COLB];
+#pragma unroll
+    for (int j = 0; j < COLB; ++j) x[j] = j0 + j < n ? p[(uint64_t)(j0 + j) * s] : (T)0;
+#pragma unroll
+    for (int j = 0; j < COLB; ++j) sum += x[j];
+  }
+  return sum;
+}
+// p[j s] <- run + p[0] + ... + p[(j-1) s] in place; returns run + the column's sum
+template <typename T>
+__device__ __forceinline__ uint64_t col_exscan(T* p, uint64_t s, uint32_t n, uint64_t run) {
+  for (uint32_t j0 = 0; j0 < n; j0 += COLB) {
+    T x[COLB];
+#pragma unroll
+    for (int j = 0; j < COLB; ++j) x[j] = j0 + j < n ? p[(uint64_t)(j0 + j) * s] : (T)0;
+#pragma unroll
+    for (int j = 0; j < COLB; ++j)
+      if (j0 + j < n) {
+        p[(uint64_t)(j0 + j) * s] = (T)run;
+        run += x[j];
+      }
+  }
+  return run;
+}
+
 // per (bucket, chunk of warps): chunk sums
 __global__ void k_colscan_a(const uint32_t* hist, int G_w, int P, int nchunk, uint64_t* part) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= P * nchunk) return;
   const int b = t % P, c = t / P;
   const int w0 = c * COLCHUNK, w1 = min(G_w, w0 + COLCHUNK);
-  uint64_t s = 0;
-  for (int w = w0; w < w1; ++w) s += hist[(uint64_t)w * P + b];
-  part[(uint64_t)c * P + b] = s;
+  part[(uint64_t)c * P + b] = col_sum(hist + (uint64_t)w0 * P + b, (uint64_t)P, (uint32_t)(w1 - w0));
 }
 // per bucket: exclusive scan over chunks, bucket totals
 __global__ void k_colscan_b(uint64_t* part, int P, int nchunk, uint64_t* tot) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= P) return;
-  uint64_t run = 0;
-  for (int c = 0; c < nchunk; ++c) {
-    uint64_t x = part[(uint64_t)c * P + b];
-    part[(uint64_t)c * P + b] = run;
-    run += x;
-  }
-  tot[b] = run;
+  tot[b] = col_exscan(part + b, (uint64_t)P, (uint32_t)nchunk, 0);
 }
 // per (bucket, chunk): exclusive prefix over warps, in place
 __global__ void k_colscan_c(uint32_t* hist, int G_w, int P, int nchunk, const uint64_t* part) {
@@ -333,12 +358,7 @@ __global__ void k_colscan_c(uint32_t* hist, int G_w, int P, int nchunk, const ui
   if (t >= P * nchunk) return;
   const int b = t % P, c = t / P;
   const int w0 = c * COLCHUNK, w1 = min(G_w, w0 + COLCHUNK);
-  uint64_t run = part[(uint64_t)c * P + b];
-  for (int w = w0; w < w1; ++w) {
-    uint32_t x = hist[(uint64_t)w * P + b];
-    hist[(uint64_t)w * P + b] = (uint32_t)run;
-    run += x;
-  }
+  col_exscan(hist + (uint64_t)w0 * P + b, (uint64_t)P, (uint32_t)(w1 - w0), part[(uint64_t)c * P + b]);
 }
 
 
@@ -540,24 +560,58 @@ __device__ __forceinline__ uint64_t mixed_key(uint64_t key) {
   return mix64(key);
 }
 
-// count sampled keys in a global open-addressing table (key 0: empty; a key
-// whose mix is 0 is never counted)
+// Count sampled keys in a global open-addressing table (key 0: empty; a key
+// whose mix is 0 is never counted).  A CTA first counts its HS_PER * 256
+// samples in a table of its own in shared memory (at most half full), then
+// adds one count per distinct key to the global table: under a Zipf law most
+// samples share a few keys, whose global entries would otherwise take one
+// atomic per warp each.
+constexpr int HS_PER = 4;
+constexpr int HS_TBITS = 11;
+
 template <int F>
-__global__ void k_hsample(const void* keyp, uint64_t n, uint64_t stride, int tbits, uint64_t* tk, uint32_t* tc) {
-  const uint64_t i = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) * stride;
-  const bool v = i < n;
-  const uint64_t m = v ? mixed_key<F>(load_key<F>(keyp, i)) : 0ull;
-  const bool want = v && m != 0;
-  const uint32_t peers = __match_any_sync(FULL, want ? m : 0ull);
-  if (!want || (int)(threadIdx.x & 31) != __ffs(peers) - 1) return;
-  uint32_t h = (uint32_t)((m * 0x9E3779B97F4A7C15ull) >> (64 - tbits));
-  for (int probe = 0; probe < (1 << tbits); ++probe) {
-    const unsigned long long prev = atomicCAS((unsigned long long*)&tk[h], 0ull, (unsigned long long)m);
-    if (prev == 0ull || prev == m) {
-      atomicAdd(&tc[h], (uint32_t)__popc(peers));
-      return;
+__global__ void __launch_bounds__(256)
+k_hsample(const void* keyp, uint64_t n, uint64_t stride, int tbits, uint64_t* tk, uint32_t* tc) {
+  constexpr int TAB = 1 << HS_TBITS;
+  static_assert(TAB >= 2 * HS_PER * 256, "the CTA table holds every sample of the CTA at most half full");
+  __shared__ unsigned long long sk[TAB];
+  __shared__ uint32_t sc[TAB];
+  for (int e = threadIdx.x; e < TAB; e += 256) { sk[e] = 0ull; sc[e] = 0u; }
+  uint64_t m[HS_PER];
+#pragma unroll
+  for (int j = 0; j < HS_PER; ++j) {
+    const uint64_t i = (((uint64_t)blockIdx.x * HS_PER + j) * 256 + threadIdx.x) * stride;
+    m[j] = i < n ? mixed_key<F>(load_key<F>(keyp, i)) : 0ull;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < HS_PER; ++j) {
+    const uint32_t peers = __match_any_sync(FULL, m[j]);
+    if (m[j] != 0ull && (int)(threadIdx.x & 31) == __ffs(peers) - 1) {
+      uint32_t h = (uint32_t)((m[j] * 0x9E3779B97F4A7C15ull) >> (64 - HS_TBITS));
+      for (int probe = 0; probe < TAB; ++probe) {
+        const unsigned long long prev = atomicCAS(&sk[h], 0ull, (unsigned long long)m[j]);
+        if (prev == 0ull || prev == m[j]) {
+          atomicAdd(&sc[h], (uint32_t)__popc(peers));
+          break;
+        }
+        h = (h + 1) & (TAB - 1);
+      }
     }
-    h = (h + 1) & ((1u << tbits) - 1);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < TAB; e += 256) {
+    const unsigned long long key = sk[e];
+    if (key == 0ull) continue;
+    uint32_t h = (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> (64 - tbits));
+    for (int probe = 0; probe < (1 << tbits); ++probe) {
+      const unsigned long long prev = atomicCAS((unsigned long long*)&tk[h], 0ull, key);
+      if (prev == 0ull || prev == key) {
+        atomicAdd(&tc[h], sc[e]);
+        break;
+      }
+      h = (h + 1) & ((1u << tbits) - 1);
+    }
   }
 }
 
@@ -659,31 +713,47 @@ k_hist2(const typename RecT<F>::type* recs, const Tile* tiles, const unsigned in
 
 // per (first-level bucket, sub-bucket): exclusive prefix over the bucket's
 // tiles.  One CTA per first-level bucket: rows of threads each take a
-// contiguous share of the tiles for every sub-bucket column (2^B2 columns),
-// the rows' sums are scanned in shared memory, then every row writes its
-// share's prefixes.
+// contiguous share of the tiles for every sub-bucket column (2^B2 <= 256
+// columns), the rows' sums are scanned in shared memory, then every row writes
+// its share's prefixes.  The sub-buckets of a bucket fill exactly the bucket's
+// range of the first-level output, so their starts are the bucket's start plus
+// the totals of the columns before them, written here with the end sentinel.
 __global__ void __launch_bounds__(1024)
-k_scan2(uint32_t* hist2, const uint32_t* tfirst, const uint32_t* tK, int P1, int B2, uint64_t* tot2) {
+k_scan2(uint32_t* hist2, const uint32_t* tfirst, const uint32_t* tK, int P1, int B2, const uint64_t* bstart1,
+        uint64_t* bstart2) {
   __shared__ uint64_t part[1024];
+  __shared__ uint64_t ctot[256];
   const int P2 = 1 << B2, rows = 1024 >> B2;
   const int b1 = blockIdx.x;
   const int col = threadIdx.x & (P2 - 1), row = threadIdx.x >> B2;
   const uint32_t f = tfirst[b1], k = tK[b1];
   const uint32_t share = (k + rows - 1) / rows;
   const uint32_t j0 = min(k, row * share), j1 = min(k, j0 + share);
-  uint64_t sum = 0;
-  for (uint32_t j = j0; j < j1; ++j) sum += hist2[(uint64_t)(f + j) * P2 + col];
-  part[threadIdx.x] = sum;
+  uint32_t* colp = hist2 + (uint64_t)(f + j0) * P2 + col;
+  part[threadIdx.x] = col_sum(colp, (uint64_t)P2, j1 - j0);
   __syncthreads();
   uint64_t run = 0;
   for (int r = 0; r < row; ++r) run += part[(r << B2) + col];
-  for (uint32_t j = j0; j < j1; ++j) {
-    const uint64_t idx = (uint64_t)(f + j) * P2 + col;
-    const uint32_t x = hist2[idx];
-    hist2[idx] = (uint32_t)run;
-    run += x;
+  run = col_exscan(colp, (uint64_t)P2, j1 - j0, run);
+  if (row == rows - 1) ctot[col] = run;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x, per = (P2 + 31) / 32;
+    const int c0 = min(P2, lane * per), c1 = min(P2, c0 + per);
+    uint64_t sum = 0;
+    for (int c = c0; c < c1; ++c) sum += ctot[c];
+    uint64_t x = sum;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint64_t y = __shfl_up_sync(FULL, x, o);
+      if (lane >= o) x += y;
+    }
+    uint64_t st = bstart1[b1] + x - sum;
+    for (int c = c0; c < c1; ++c) {
+      bstart2[((uint64_t)b1 << B2) + c] = st;
+      st += ctot[c];
+    }
+    if (b1 == P1 - 1 && lane == 31) bstart2[(uint64_t)P1 << B2] = bstart1[P1];
   }
-  if (row == rows - 1) tot2[((uint64_t)b1 << B2) + col] = run;
 }
 
 template <int F>
@@ -1672,8 +1742,8 @@ k_fold(const typename RecT<F>::type* recs, const Tile* units, const unsigned int
 }
 
 // Groups of up to GC consecutive items of every bucket still holding K >= 2
-// items; a bucket that ends up with one group is finalised by it.
-// The buckets that more than one unit folds, listed once after k_fold (in
+// items are combined level by level; a bucket that ends up with one group is
+// finalised by it.  The buckets that more than one unit folds, listed once after k_fold (in
 // any order) with their unit counts and first units; the combine levels work
 // on this short list instead of on every bucket.
 __global__ void k_list_multi(const uint32_t* K, const uint32_t* first, int P, unsigned int* m, uint32_t* ids,
@@ -1686,26 +1756,88 @@ __global__ void k_list_multi(const uint32_t* K, const uint32_t* first, int P, un
   F0[i] = first[b];
 }
 
-__global__ void k_count_groups(const uint32_t* K_in, const unsigned int* m, uint32_t* K_out) {
-  const unsigned int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= *m) return;
-  const uint32_t k = K_in[i];
-  K_out[i] = k >= 2 ? (k + GC - 1) / GC : 0u;
-}
-
-__global__ void k_emit_groups(const uint32_t* first_in, const uint32_t* K_in, const unsigned int* m,
-                              const uint32_t* first_out, const uint32_t* K_out, const uint32_t* ids, Group* groups) {
-  const unsigned int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= *m) return;
-  const uint32_t k = K_in[i], g = K_out[i];
-  for (uint32_t j = 0; j < g; ++j) {
-    Group G;
-    G.bucket = ids[i];
-    G.first = first_in[i] + j * GC;
-    G.cnt = min((uint32_t)GC, k - j * GC);
-    G.k = j; G.K = g; G.pad = 0;
-    groups[first_out[i] + j] = G;
+// One CTA builds the next level's groups of every listed bucket: K_out[i] =
+// ceil(K_in[i] / GC) groups for a bucket of K_in[i] >= 2 items (none for
+// fewer), first_out[i] their exclusive prefix, the groups themselves and
+// their number.  Chunks of GRP_CH entries are staged in shared memory (padded
+// by one word per 32 entries) and every thread scans a run of GRP_RUN.
+constexpr int GRP_RUN = 8;
+constexpr int GRP_CH = GRP_RUN * 1024;
+__global__ void __launch_bounds__(1024)
+k_groups(const uint32_t* first_in, const uint32_t* K_in, const unsigned int* m, const uint32_t* ids, uint32_t* first_out,
+         uint32_t* K_out, Group* groups, unsigned int* n_groups) {
+  __shared__ uint32_t sg[GRP_CH + GRP_CH / 32];
+  __shared__ uint32_t wsum[32];
+  const unsigned int M = *m;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  uint32_t carry = 0;
+  for (unsigned int base = 0; base < M; base += GRP_CH) {
+    const int len = (int)min((unsigned int)GRP_CH, M - base);
+    uint32_t kk[GRP_RUN];
+#pragma unroll
+    for (int r = 0; r < GRP_RUN; ++r) {
+      const int i = t + r * 1024;
+      kk[r] = i < len ? K_in[base + i] : 0u;
+      if (i < len) sg[i + (i >> 5)] = kk[r] >= 2 ? (kk[r] + GC - 1) / GC : 0u;
+    }
+    __syncthreads();
+    const int i0 = t * GRP_RUN;
+    uint32_t sum = 0;
+#pragma unroll
+    for (int j = 0; j < GRP_RUN; ++j) {
+      const int i = i0 + j;
+      sum += i < len ? sg[i + (i >> 5)] : 0u;
+    }
+    uint32_t x = sum;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(FULL, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    if (w == 0) {
+      uint32_t z = wsum[lane];
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, z, o);
+        if (lane >= o) z += y;
+      }
+      wsum[lane] = z;
+    }
+    __syncthreads();
+    uint32_t run = carry + x - sum + (w ? wsum[w - 1] : 0u);
+#pragma unroll
+    for (int j = 0; j < GRP_RUN; ++j) {
+      const int i = i0 + j;
+      if (i < len) {
+        const uint32_t g = sg[i + (i >> 5)];
+        sg[i + (i >> 5)] = run;
+        run += g;
+      }
+    }
+    carry += wsum[31];
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < GRP_RUN; ++r) {
+      const int i = t + r * 1024;
+      if (i >= len) continue;
+      const unsigned int e = base + i;
+      const uint32_t k = kk[r], g = k >= 2 ? (k + GC - 1) / GC : 0u, first = sg[i + (i >> 5)];
+      K_out[e] = g;
+      first_out[e] = first;
+      if (!g) continue;
+      const uint32_t f0 = first_in[e], bucket = ids[e];
+      for (uint32_t j = 0; j < g; ++j) {
+        Group G;
+        G.bucket = bucket;
+        G.first = f0 + j * GC;
+        G.cnt = min((uint32_t)GC, k - j * GC);
+        G.k = j; G.K = g; G.pad = 0;
+        groups[first + j] = G;
+      }
+    }
+    __syncthreads();
   }
+  if (t == 0) *n_groups = carry;
 }
 
 struct CombineShared {
@@ -1713,6 +1845,7 @@ struct CombineShared {
   SlotTable T;
   OuterTable U;
   uint32_t pass_bits[64], pass_val[64];
+  Item items[GC];            // the group's items
   int npass;
   uint64_t out_off;
   uint32_t out_cnt;
@@ -1737,10 +1870,11 @@ k_combine(const Item* items_in, const Pair* pool_in, const Group* groups, const 
     if (g >= ng) break;
     const Group G = groups[g];
     const bool final_ = G.K == 1;
+    if (threadIdx.x < G.cnt) S.items[threadIdx.x] = items_in[G.first + threadIdx.x];
     __syncthreads();
     if (threadIdx.x == 0) {
       uint64_t total = 0;
-      for (uint32_t j = 0; j < G.cnt; ++j) total += items_in[G.first + j].cnt;
+      for (uint32_t j = 0; j < G.cnt; ++j) total += S.items[j].cnt;
       S.npass = 1; S.pass_bits[0] = 0; S.pass_val[0] = 0;
       S.out_cnt = 0;
       S.out_off = final_ ? 0 : atomicAdd(&p.acc->pair_top[dst], (unsigned long long)total);
@@ -1754,10 +1888,17 @@ k_combine(const Item* items_in, const Pair* pool_in, const Group* groups, const 
       const uint32_t val = S.pass_val[S.npass - 1];
       reset_table(S.T);
       __syncthreads();
+      // items in order (a key's maps compose in trace order); the first pair of
+      // a thread in the next item is loaded while this item is inserted
+      const uint32_t tid = threadIdx.x;
+      Pair nx{0ull, 0ull};
+      if (G.cnt && tid < S.items[0].cnt) nx = pool_in[S.items[0].off + tid];
       for (uint32_t j = 0; j < G.cnt; ++j) {
-        const Item I = items_in[G.first + j];
-        for (uint32_t q = threadIdx.x; q < I.cnt; q += blockDim.x) {
-          const Pair pr = pool_in[I.off + q];
+        const Item I = S.items[j];
+        Pair pr = nx;
+        if (j + 1 < G.cnt && tid < S.items[j + 1].cnt) nx = pool_in[S.items[j + 1].off + tid];
+        for (uint32_t q = tid; q < I.cnt; q += blockDim.x) {
+          if (q != tid) pr = pool_in[I.off + q];
           if (!in_pass(pr.key, bits, val)) continue;
           const int slot = find_or_insert(S.T, pr.key, p.acc, [&](unsigned int s) { S.smap[s] = IDENTITY_MAP; });
           if (slot >= 0) S.smap[slot] = apply_map(S.smap[slot], pr.map, ns);
@@ -1833,7 +1974,7 @@ struct Plan {
   int levels;
   size_t rec_bytes;
   // workspace offsets
-  size_t o_acc, o_hist, o_part, o_tot1, o_bstart1, o_recA, o_recB, o_tiles2, o_tf2, o_tk2, o_hist2, o_tot2,
+  size_t o_acc, o_hist, o_part, o_tot1, o_bstart1, o_recA, o_recB, o_tiles2, o_tf2, o_tk2, o_hist2,
       o_bstart2, o_units, o_uf, o_uk, o_items0, o_items1, o_groups, o_gf0, o_gk0, o_gf1, o_gk1, o_pool0,
       o_pool1, o_res, o_hkey, o_hpred, o_hts, o_uend, o_htk, o_htc, o_hcnt, o_hlist, o_mids, o_mk, o_mf, total;
 };
@@ -1908,7 +2049,6 @@ static Plan make_plan(const rv_formula* f, uint64_t n, int host_input, const rv_
   pl.o_tf2 = pl.B2 ? take((size_t)pl.P1 * 4) : 0;
   pl.o_tk2 = pl.B2 ? take((size_t)pl.P1 * 4) : 0;
   pl.o_hist2 = pl.B2 ? take(pl.max_tiles2 * ((size_t)1 << pl.B2e) * 4) : 0;
-  pl.o_tot2 = pl.B2 ? take((size_t)pl.P * 8) : 0;
   pl.o_bstart2 = pl.B2 ? take((size_t)(pl.P + 1) * 8) : pl.o_bstart1;
   pl.o_units = take(pl.max_units * sizeof(Tile));
   pl.o_uf = take((size_t)pl.P * 4);
@@ -2006,7 +2146,6 @@ static rv_status launch_all(const Plan& pl, const rv_formula* f, const void* key
       uint32_t* tf2 = (uint32_t*)(ws + pl.o_tf2);
       uint32_t* tk2 = (uint32_t*)(ws + pl.o_tk2);
       uint32_t* hist2 = (uint32_t*)(ws + pl.o_hist2);
-      uint64_t* tot2 = (uint64_t*)(ws + pl.o_tot2);
       uint64_t* bstart2 = (uint64_t*)(ws + pl.o_bstart2);
       Rec* recB = (Rec*)(ws + pl.o_recB);
       RV_LAUNCH("k_count_tiles", k_count_tiles, (pl.P1 + 255) / 256, 256, 0, s, bstart1, pl.P1, pl.tile2, tk2);
@@ -2024,14 +2163,14 @@ static rv_status launch_all(const Plan& pl, const rv_formula* f, const void* key
         RV_CU(cudaMemsetAsync(hcnt, 0, (size_t)pl.P1 * 4, s));
         const uint64_t samples = (n + pl.hstride - 1) / pl.hstride;
         const uint32_t thresh = (uint32_t)std::max<uint64_t>(8, HRECORDS / pl.hstride);
-        RV_LAUNCH("k_hsample", k_hsample<F>, (int)((samples + 255) / 256), 256, 0, s, key, n, pl.hstride, pl.htbits, htk, htc);
+        RV_LAUNCH("k_hsample", k_hsample<F>, (int)((samples + HS_PER * 256 - 1) / (HS_PER * 256)), 256, 0, s, key, n, pl.hstride,
+                  pl.htbits, htk, htc);
         RV_LAUNCH("k_hpick", k_hpick<F>, (1 << pl.htbits) / 256, 256, 0, s, htk, htc, pl.htbits, thresh, pl.B1, pl.hmax, hcnt,
                   hlist);
         hv = HeavyDev{hcnt, hlist, pl.hmax};
       }
       RV_LAUNCH("k_hist2", k_hist2<F>, t2_blocks, SC_WARPS * 32, 0, s, recA, tiles2, &acc->n_tiles2, pl.B1, pl.B2, hist2, hv);
-      RV_LAUNCH("k_scan2", k_scan2, pl.P1, 1024, 0, s, hist2, tf2, tk2, pl.P1, pl.B2e, tot2);
-      RV_LAUNCH("k_bucket_scan", k_scan<uint64_t>, 1, 1024, scan_smem<uint64_t>(), s, tot2, pl.P, bstart2, bstart2 + pl.P);
+      RV_LAUNCH("k_scan2", k_scan2, pl.P1, 1024, 0, s, hist2, tf2, tk2, pl.P1, pl.B2e, bstart1, bstart2);
       if (F == FMT_K32)
         RV_LAUNCH("k_scatter2", k_scatter2<F>, t2_blocks, SC_WARPS * 32, 0, s, recA, tiles2, &acc->n_tiles2, pl.B1, pl.B2, hist2,
                   bstart2, recB, hv);
@@ -2072,11 +2211,8 @@ static rv_status launch_all(const Plan& pl, const rv_formula* f, const void* key
     for (int l = 0; l < pl.levels; ++l) {
       const int dst = (l + 1) & 1;
       RV_CU(cudaMemsetAsync(&acc->pair_top[dst], 0, sizeof(unsigned long long), s));
-      RV_LAUNCH("k_count_groups", k_count_groups, (pl.P + 255) / 256, 256, 0, s, kin, &acc->n_multi, gk[l & 1]);
-      RV_LAUNCH("k_scan_u32", k_scan<uint32_t>, 1, 1024, scan_smem<uint32_t>(), s, gk[l & 1], pl.P, gf[l & 1], &acc->n_groups[l],
-                &acc->n_multi);
-      RV_LAUNCH("k_emit_groups", k_emit_groups, (pl.P + 255) / 256, 256, 0, s, fin, kin, &acc->n_multi, gf[l & 1], gk[l & 1], mids,
-                groups);
+      RV_LAUNCH("k_groups", k_groups, 1, 1024, 0, s, fin, kin, &acc->n_multi, mids, gf[l & 1], gk[l & 1], groups,
+                &acc->n_groups[l]);
       const int cgrid = (int)std::min<uint64_t>(pl.max_units / GC + pl.P, (uint64_t)num_sms() * 2);
       RV_LAUNCH("k_combine", k_combine<F>, cgrid, FOLD_THREADS, sizeof(CombineShared), s, iin, pin, groups, &acc->n_groups[l], &acc->next_group[l], p,
                                                                       iout, pout, dst);

@@ -247,3 +247,18 @@ def test_zipf_heads_in_own_sub_buckets(rv, torch_cuda, opts):
     # in sub-buckets of their own (or not, with no_heavy); both must match
     tr = synth.socket_trace(3_000_000, 20_000, pending_frac=0.03, zipf_s=1.1, seed=31)
     _check(rv, torch_cuda, C1, tr.codes, tr.key, tr.pred, opts=opts)
+
+
+def test_many_multi_unit_buckets(rv, torch_cuda):
+    # 2^14 light sub-buckets of about 300 records cut into 256-record units:
+    # over 8192 buckets are folded by two units or more, so the bucket list of
+    # every combine level spans more than one staged chunk; one planted
+    # binding of 40k events is folded by over 150 units (two combine levels)
+    tr = synth.socket_trace(5_000_000, 1_000_000, pending_frac=0.03, seed=41)
+    key = tr.key.copy()
+    rng = np.random.default_rng(42)
+    key[rng.choice(len(key), size=40_000, replace=False)] = key[0]
+    top = _fmix32(key) >> np.uint32(32 - 14)
+    assert (np.bincount(top, minlength=1 << 14) > 256).sum() > 8192
+    opts = {"bucket_bits": 8, "sub_bucket_bits": 6, "unit_records": 256}
+    _check(rv, torch_cuda, C1, tr.codes, key, tr.pred, opts=opts)
