@@ -561,13 +561,14 @@ __device__ __forceinline__ uint64_t mixed_key(uint64_t key) {
 }
 
 // Count sampled keys in a global open-addressing table (key 0: empty; a key
-// whose mix is 0 is never counted).  A CTA first counts its HS_PER * 256
+// whose mix is 0 is never counted).  The sample is HS_RUN consecutive events
+// out of every HS_RUN * stride (the same rate as one event in stride, from
+// far fewer scattered memory sectors).  A CTA first counts its HS_PER * 256
 // samples in a table of its own in shared memory (at most half full), then
-// adds one count per distinct key to the global table: under a Zipf law most
-// samples share a few keys, whose global entries would otherwise take one
-// atomic per warp each.
+// adds one count per distinct key to the global table.
 constexpr int HS_PER = 4;
 constexpr int HS_TBITS = 11;
+constexpr int HS_RUN = 8;
 
 template <int F>
 __global__ void __launch_bounds__(256)
@@ -580,7 +581,8 @@ k_hsample(const void* keyp, uint64_t n, uint64_t stride, int tbits, uint64_t* tk
   uint64_t m[HS_PER];
 #pragma unroll
   for (int j = 0; j < HS_PER; ++j) {
-    const uint64_t i = (((uint64_t)blockIdx.x * HS_PER + j) * 256 + threadIdx.x) * stride;
+    const uint64_t smp = ((uint64_t)blockIdx.x * HS_PER + j) * 256 + threadIdx.x;
+    const uint64_t i = smp / HS_RUN * (HS_RUN * stride) + smp % HS_RUN;
     m[j] = i < n ? mixed_key<F>(load_key<F>(keyp, i)) : 0ull;
   }
   __syncthreads();
@@ -712,29 +714,71 @@ k_hist2(const typename RecT<F>::type* recs, const Tile* tiles, const unsigned in
 }
 
 // per (first-level bucket, sub-bucket): exclusive prefix over the bucket's
-// tiles.  One CTA per first-level bucket: rows of threads each take a
-// contiguous share of the tiles for every sub-bucket column (2^B2 <= 256
-// columns), the rows' sums are scanned in shared memory, then every row writes
-// its share's prefixes.  The sub-buckets of a bucket fill exactly the bucket's
-// range of the first-level output, so their starts are the bucket's start plus
-// the totals of the columns before them, written here with the end sentinel.
+// tiles.  A bucket's tiles are cut into up to SCAN2_S slices of at least
+// SCAN2_MIN tiles (a Zipf head's bucket holds over a thousand tiles, more than
+// one SM moves quickly), one CTA per slice.  k_scan2_sums writes every slice's
+// column sums when there are several; in k_scan2, rows of threads each take a
+// contiguous share of the slice's tiles for every sub-bucket column (2^B2 <=
+// 256 columns), the rows' sums are scanned in shared memory on top of the
+// earlier slices' sums, then every row writes its share's prefixes.  The
+// sub-buckets of a bucket fill exactly the bucket's range of the first-level
+// output, so their starts are the bucket's start plus the totals of the
+// columns before them, written by the last slice with the end sentinel.
+constexpr int SCAN2_S = 8;
+constexpr uint32_t SCAN2_MIN = 128;
+__device__ __forceinline__ uint32_t scan2_slices(uint32_t k) {
+  return min((uint32_t)SCAN2_S, max(1u, (k + SCAN2_MIN - 1) / SCAN2_MIN));
+}
+// tiles [j0, j1) of row `row` (of `rows`) in slice sl (of ns) of k tiles
+__device__ __forceinline__ void scan2_share(uint32_t k, uint32_t sl, uint32_t ns, int row, int rows, uint32_t& j0,
+                                            uint32_t& j1) {
+  const uint32_t s0 = (uint32_t)((uint64_t)k * sl / ns), s1 = (uint32_t)((uint64_t)k * (sl + 1) / ns);
+  const uint32_t share = (s1 - s0 + rows - 1) / rows;
+  j0 = min(s1, s0 + row * share);
+  j1 = min(s1, j0 + share);
+}
+
 __global__ void __launch_bounds__(1024)
-k_scan2(uint32_t* hist2, const uint32_t* tfirst, const uint32_t* tK, int P1, int B2, const uint64_t* bstart1,
-        uint64_t* bstart2) {
+k_scan2_sums(const uint32_t* hist2, const uint32_t* tfirst, const uint32_t* tK, int B2, uint32_t* ssum) {
+  __shared__ uint64_t part[1024];
+  const int P2 = 1 << B2, rows = 1024 >> B2;
+  const int b1 = blockIdx.x / SCAN2_S;
+  const uint32_t sl = blockIdx.x % SCAN2_S;
+  const uint32_t f = tfirst[b1], k = tK[b1], ns = scan2_slices(k);
+  if (ns == 1 || sl >= ns) return;
+  const int col = threadIdx.x & (P2 - 1), row = threadIdx.x >> B2;
+  uint32_t j0, j1;
+  scan2_share(k, sl, ns, row, rows, j0, j1);
+  part[threadIdx.x] = col_sum(hist2 + (uint64_t)(f + j0) * P2 + col, (uint64_t)P2, j1 - j0);
+  __syncthreads();
+  if (row == 0) {
+    uint64_t sum = 0;
+    for (int r = 0; r < rows; ++r) sum += part[(r << B2) + col];
+    ssum[(uint64_t)blockIdx.x * P2 + col] = (uint32_t)sum;
+  }
+}
+
+__global__ void __launch_bounds__(1024)
+k_scan2(uint32_t* hist2, const uint32_t* tfirst, const uint32_t* tK, int P1, int B2, const uint32_t* ssum,
+        const uint64_t* bstart1, uint64_t* bstart2) {
   __shared__ uint64_t part[1024];
   __shared__ uint64_t ctot[256];
   const int P2 = 1 << B2, rows = 1024 >> B2;
-  const int b1 = blockIdx.x;
+  const int b1 = blockIdx.x / SCAN2_S;
+  const uint32_t sl = blockIdx.x % SCAN2_S;
+  const uint32_t f = tfirst[b1], k = tK[b1], ns = scan2_slices(k);
+  if (sl >= ns) return;
   const int col = threadIdx.x & (P2 - 1), row = threadIdx.x >> B2;
-  const uint32_t f = tfirst[b1], k = tK[b1];
-  const uint32_t share = (k + rows - 1) / rows;
-  const uint32_t j0 = min(k, row * share), j1 = min(k, j0 + share);
+  uint32_t j0, j1;
+  scan2_share(k, sl, ns, row, rows, j0, j1);
   uint32_t* colp = hist2 + (uint64_t)(f + j0) * P2 + col;
   part[threadIdx.x] = col_sum(colp, (uint64_t)P2, j1 - j0);
   __syncthreads();
   uint64_t run = 0;
+  for (uint32_t q = 0; q < sl; ++q) run += ssum[((uint64_t)b1 * SCAN2_S + q) * P2 + col];
   for (int r = 0; r < row; ++r) run += part[(r << B2) + col];
   run = col_exscan(colp, (uint64_t)P2, j1 - j0, run);
+  if (sl != ns - 1) return;           // uniform across the CTA
   if (row == rows - 1) ctot[col] = run;
   __syncthreads();
   if (threadIdx.x < 32) {
@@ -1974,7 +2018,7 @@ struct Plan {
   int levels;
   size_t rec_bytes;
   // workspace offsets
-  size_t o_acc, o_hist, o_part, o_tot1, o_bstart1, o_recA, o_recB, o_tiles2, o_tf2, o_tk2, o_hist2,
+  size_t o_acc, o_hist, o_part, o_tot1, o_bstart1, o_recA, o_recB, o_tiles2, o_tf2, o_tk2, o_hist2, o_ssum2,
       o_bstart2, o_units, o_uf, o_uk, o_items0, o_items1, o_groups, o_gf0, o_gk0, o_gf1, o_gk1, o_pool0,
       o_pool1, o_res, o_hkey, o_hpred, o_hts, o_uend, o_htk, o_htc, o_hcnt, o_hlist, o_mids, o_mk, o_mf, total;
 };
@@ -2049,6 +2093,7 @@ static Plan make_plan(const rv_formula* f, uint64_t n, int host_input, const rv_
   pl.o_tf2 = pl.B2 ? take((size_t)pl.P1 * 4) : 0;
   pl.o_tk2 = pl.B2 ? take((size_t)pl.P1 * 4) : 0;
   pl.o_hist2 = pl.B2 ? take(pl.max_tiles2 * ((size_t)1 << pl.B2e) * 4) : 0;
+  pl.o_ssum2 = pl.B2 ? take((size_t)pl.P1 * SCAN2_S * ((size_t)1 << pl.B2e) * 4) : 0;
   pl.o_bstart2 = pl.B2 ? take((size_t)(pl.P + 1) * 8) : pl.o_bstart1;
   pl.o_units = take(pl.max_units * sizeof(Tile));
   pl.o_uf = take((size_t)pl.P * 4);
@@ -2146,6 +2191,7 @@ static rv_status launch_all(const Plan& pl, const rv_formula* f, const void* key
       uint32_t* tf2 = (uint32_t*)(ws + pl.o_tf2);
       uint32_t* tk2 = (uint32_t*)(ws + pl.o_tk2);
       uint32_t* hist2 = (uint32_t*)(ws + pl.o_hist2);
+      uint32_t* ssum2 = (uint32_t*)(ws + pl.o_ssum2);
       uint64_t* bstart2 = (uint64_t*)(ws + pl.o_bstart2);
       Rec* recB = (Rec*)(ws + pl.o_recB);
       RV_LAUNCH("k_count_tiles", k_count_tiles, (pl.P1 + 255) / 256, 256, 0, s, bstart1, pl.P1, pl.tile2, tk2);
@@ -2161,7 +2207,7 @@ static rv_status launch_all(const Plan& pl, const rv_formula* f, const void* key
         RV_CU(cudaMemsetAsync(htk, 0, ((size_t)1 << pl.htbits) * 8, s));
         RV_CU(cudaMemsetAsync(htc, 0, ((size_t)1 << pl.htbits) * 4, s));
         RV_CU(cudaMemsetAsync(hcnt, 0, (size_t)pl.P1 * 4, s));
-        const uint64_t samples = (n + pl.hstride - 1) / pl.hstride;
+        const uint64_t samples = (n + HS_RUN * pl.hstride - 1) / (HS_RUN * pl.hstride) * HS_RUN;
         const uint32_t thresh = (uint32_t)std::max<uint64_t>(8, HRECORDS / pl.hstride);
         RV_LAUNCH("k_hsample", k_hsample<F>, (int)((samples + HS_PER * 256 - 1) / (HS_PER * 256)), 256, 0, s, key, n, pl.hstride,
                   pl.htbits, htk, htc);
@@ -2170,7 +2216,8 @@ static rv_status launch_all(const Plan& pl, const rv_formula* f, const void* key
         hv = HeavyDev{hcnt, hlist, pl.hmax};
       }
       RV_LAUNCH("k_hist2", k_hist2<F>, t2_blocks, SC_WARPS * 32, 0, s, recA, tiles2, &acc->n_tiles2, pl.B1, pl.B2, hist2, hv);
-      RV_LAUNCH("k_scan2", k_scan2, pl.P1, 1024, 0, s, hist2, tf2, tk2, pl.P1, pl.B2e, bstart1, bstart2);
+      RV_LAUNCH("k_scan2_sums", k_scan2_sums, pl.P1 * SCAN2_S, 1024, 0, s, hist2, tf2, tk2, pl.B2e, ssum2);
+      RV_LAUNCH("k_scan2", k_scan2, pl.P1 * SCAN2_S, 1024, 0, s, hist2, tf2, tk2, pl.P1, pl.B2e, ssum2, bstart1, bstart2);
       if (F == FMT_K32)
         RV_LAUNCH("k_scatter2", k_scatter2<F>, t2_blocks, SC_WARPS * 32, 0, s, recA, tiles2, &acc->n_tiles2, pl.B1, pl.B2, hist2,
                   bstart2, recB, hv);
