@@ -58,12 +58,19 @@ constexpr uint64_t EMPTY_KEY = ~0ull;
 constexpr unsigned FULL = 0xFFFFFFFFu;
 constexpr int SPIN_LIMIT = 1 << 22;
 constexpr int BATCH = 16;      // rounds of 32 events whose loads are issued together
-constexpr int HBATCH = 8;      // the same for the level-2 histogram, which keeps more warps resident
+constexpr int HVEC = 4;        // 16-byte loads in flight per lane in the level-2 histogram
 
 struct Tile { uint32_t bucket, k, K, pad; uint64_t begin, end; };
 struct Item { uint64_t off; uint32_t cnt, pad; };
 struct Group { uint32_t bucket, first, cnt, k, K, pad; };
 struct Pair { uint64_t key, map; };
+
+// record e of a 16-byte word (little-endian): four 32-bit or two 64-bit records
+template <typename Rec>
+__device__ __forceinline__ uint64_t word_rec(const uint4& x, int e) {
+  if constexpr (sizeof(Rec) == 4) return e == 0 ? x.x : e == 1 ? x.y : e == 2 ? x.z : x.w;
+  else return e == 0 ? ((uint64_t)x.y << 32 | x.x) : ((uint64_t)x.w << 32 | x.z);
+}
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
   uint32_t m;
@@ -692,22 +699,32 @@ k_hist2(const typename RecT<F>::type* recs, const Tile* tiles, const unsigned in
   const uint64_t* hl = hl_all[wl];
   const uint8_t* filt = filt_all[wl];
   const int sh = sub_shift<F>(B1, B2);
-  for (uint64_t base = tl.begin; base < tl.end; base += 32 * HBATCH) {
-    typename RecT<F>::type r[HBATCH];
-    uint32_t b[HBATCH];
+  // Counts do not depend on the order, so the tile is read in 16-byte words
+  // (HVEC in flight per lane); the records before the first 16-byte boundary
+  // and after the last one are read one per lane.
+  typedef typename RecT<F>::type Rec;
+  constexpr int VEC = 16 / sizeof(Rec);
+  const Rec* rb = recs + tl.begin;
+  const uint64_t len = tl.end - tl.begin;
+  const uint64_t head = min(len, (uint64_t)(((16u - ((uint32_t)(uintptr_t)rb & 15u)) & 15u) / sizeof(Rec)));
+  const uint64_t nv = (len - head) / VEC, tail = head + nv * VEC;
+  if ((uint64_t)lane < head) atomicAdd(&cnt[sub_of((uint64_t)rb[lane], sh, P2L, hl, filt, nh)], 1u);
+  if ((uint64_t)lane < len - tail) atomicAdd(&cnt[sub_of((uint64_t)rb[tail + lane], sh, P2L, hl, filt, nh)], 1u);
+  const uint4* v = reinterpret_cast<const uint4*>(rb + head);
+  for (uint64_t q0 = 0; q0 < nv; q0 += 32 * HVEC) {
+    uint4 x[HVEC];
 #pragma unroll
-    for (int j = 0; j < HBATCH; ++j) {   // all loads first, so that they are in flight together
-      const uint64_t i = base + j * 32 + lane;
-      r[j] = i < tl.end ? recs[i] : 0;
+    for (int j = 0; j < HVEC; ++j) {   // all loads first, so that they are in flight together
+      const uint64_t q = q0 + j * 32 + lane;
+      x[j] = q < nv ? v[q] : make_uint4(0u, 0u, 0u, 0u);
     }
 #pragma unroll
-    for (int j = 0; j < HBATCH; ++j) {
-      const uint64_t i = base + j * 32 + lane;
-      b[j] = i < tl.end ? sub_of((uint64_t)r[j], sh, P2L, hl, filt, nh) : 0xFFFFFFFFu;
-    }
+    for (int j = 0; j < HVEC; ++j) {
+      if (q0 + j * 32 + lane >= nv) continue;
 #pragma unroll
-    for (int j = 0; j < HBATCH; ++j)
-      if (b[j] != 0xFFFFFFFFu) atomicAdd(&cnt[b[j]], 1u);
+      for (int e = 0; e < VEC; ++e)
+        atomicAdd(&cnt[sub_of(word_rec<Rec>(x[j], e), sh, P2L, hl, filt, nh)], 1u);
+    }
   }
   __syncwarp();
   for (int b = lane; b < P2; b += 32) hist2[(uint64_t)tile * P2 + b] = cnt[b];
