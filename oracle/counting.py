@@ -38,8 +38,9 @@ it (the same list of readings is kept in the design notes):
    (one F child makes it F), which this reproduces.
  * N = 0 (a root with no bindings) is decided by the same integer comparisons.
 
-Parity of these readings beyond the worked example, Table 1, the A_{=1} rule
-and the case-study thresholds is unpinned: the paper gives no further values.
+Parity unpinned: these readings beyond the worked example, Table 1, the
+A_{=1} rule and the case-study thresholds have no values in the paper to be
+checked against.
 """
 from __future__ import annotations
 
