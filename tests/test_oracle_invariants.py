@@ -81,6 +81,58 @@ def test_equality_readings():
             assert ra.root == rb.root and ra.verdicts == rb.verdicts
 
 
+def _count_vectors(max_n):
+    """Every vector of six child-verdict counts with 1 <= N <= max_n."""
+    def rec(i, left):
+        if i == 5:
+            yield (left,)
+            return
+        for k in range(left + 1):
+            for rest in rec(i + 1, left - k):
+                yield (k,) + rest
+    for N in range(1, max_n + 1):
+        yield from rec(0, N)
+
+
+def _check_ladder_monotone():
+    # B6 is a chain (F < Fc < Fp < Tp < Tc < T, Sec. 2.4.4): moving one child
+    # up the chain, with the number of children fixed, makes more of them count
+    # as true at every level of certainty, so it can never lower the verdict of
+    # a '>=' or '>' node nor raise that of a '<=' or '<' node
+    consts = {"E": [Fraction(k) for k in range(4)],
+              "A": [Fraction(0), Fraction(1, 4), Fraction(1, 3), Fraction(1, 2), Fraction(2, 3), Fraction(1)]}
+    moves = 0
+    for kind in ("E", "A"):
+        for op in (">=", ">", "<=", "<"):
+            for c in consts[kind]:
+                q = counting_quant(kind, op, c)
+                for v in _count_vectors(4):
+                    b0 = counting.valuate(q, list(v))
+                    for i in range(6):
+                        if not v[i]:
+                            continue
+                        for j in range(i + 1, 6):
+                            w = list(v)
+                            w[i] -= 1
+                            w[j] += 1
+                            b1 = counting.valuate(q, w)
+                            moves += 1
+                            if op in (">=", ">"):
+                                assert b1 >= b0, (kind, op, c, v, i, j, b0, b1)
+                            else:
+                                assert b1 <= b0, (kind, op, c, v, i, j, b0, b1)
+    assert moves > 10000
+
+
+def counting_quant(kind, op, const):
+    from oracle.formula import Quantifier
+    return Quantifier(kind, op, const, "x", "p")
+
+
+def test_ladder_monotone_in_child_verdicts():
+    _check_ladder_monotone()
+
+
 # ------------------------------------------------------------------ planted mistakes
 def _weak_next(f, letters, ap_truth, memo=None):
     if f[0] == "X":
@@ -137,3 +189,23 @@ def test_ladder_mutation_caught_by_threshold_pin(monkeypatch):
     with pytest.raises(AssertionError):
         pins.test_case_study1_threshold()
     assert Fraction(1) == 1
+
+
+def test_ladder_wrong_index_caught_by_monotonicity(monkeypatch):
+    # a '>=' ladder whose Tc rung sums the Fc children instead of the Tc ones
+    # must break the monotonicity invariant
+    orig = counting._ladder
+
+    def wrong_index(kind, op, const, v):
+        b = orig(kind, op, const, v)
+        if op not in (">=", ">") or b == T:
+            return b
+        N = sum(v)
+        if counting.constraint(kind, op, const, v[T] + v[counting.FC], N):
+            return counting.TC
+        if b == counting.TC:          # the rung the right sum satisfied, now missed
+            return counting.TP
+        return b
+    monkeypatch.setattr(counting, "_ladder", wrong_index)
+    with pytest.raises(AssertionError):
+        _check_ladder_monotone()
