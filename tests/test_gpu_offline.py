@@ -262,3 +262,23 @@ def test_many_multi_unit_buckets(rv, torch_cuda):
     assert (np.bincount(top, minlength=1 << 14) > 256).sum() > 8192
     opts = {"bucket_bits": 8, "sub_bucket_bits": 6, "unit_records": 256}
     _check(rv, torch_cuda, C1, tr.codes, key, tr.pred, opts=opts)
+
+
+def test_level2_scan_in_slices(rv, torch_cuda):
+    # 40 keys that share one first-level bucket (equal top 8 bits of the mixed
+    # key) hold 1.2e6 events: that bucket's 147 level-2 tiles are scanned by
+    # two CTAs, the slice sums of the first carried into the second; the keys
+    # are heavy, so both light and heavy sub-bucket columns are non-empty
+    rng = np.random.default_rng(51)
+    cand = rng.integers(0, 2**32, size=200_000, dtype=np.uint64).astype(np.uint32)
+    top = _fmix32(cand) >> np.uint32(24)
+    vals, counts = np.unique(top, return_counts=True)
+    same = np.unique(cand[top == vals[np.argmax(counts)]])[:40]
+    assert len(same) == 40
+    key = rng.choice(same, size=1_200_000)
+    noise = rng.integers(0, 2**32, size=100_000, dtype=np.uint64).astype(np.uint32)
+    key = np.insert(key, rng.integers(0, len(key), size=len(noise)), noise)
+    assert (_fmix32(key) >> np.uint32(24) == vals[np.argmax(counts)]).sum() > 129 * 8192
+    pred = rng.integers(0, 3, size=len(key)).astype(np.uint8)
+    for opts in [{"sub_bucket_bits": 3}, {"sub_bucket_bits": 3, "no_heavy": 1}]:
+        _check(rv, torch_cuda, C1, synth.SOCKET_CODES, key, pred, opts=opts)
