@@ -41,7 +41,8 @@ it (the same list of readings is kept in the design notes):
 Parity unpinned: these readings beyond the worked example, Table 1, the
 A_{=1} rule and the case-study thresholds have no values in the paper to be
 checked against; the tests only hold them to the order of B6 (moving a child
-up the chain never lowers a '>=' or '>' node, nor raises a '<=' or '<' one).
+up the chain never lowers a '>=' or '>' node, nor raises a '<=' or '<' one)
+and to negation (a negated constraint gives the dual verdict).
 """
 from __future__ import annotations
 

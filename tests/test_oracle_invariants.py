@@ -133,6 +133,28 @@ def test_ladder_monotone_in_child_verdicts():
     _check_ladder_monotone()
 
 
+def _check_negation_duality():
+    # a node whose constraint is negated (>= and <, > and <=) decides the
+    # negated proposition, so its verdict is the dual one in B6 (T <-> F,
+    # Tc <-> Fc, Tp <-> Fp; index b <-> 5 - b), as LTL4 is for negated formulas
+    consts = {"E": [Fraction(k) for k in range(5)],
+              "A": [Fraction(0), Fraction(1, 4), Fraction(1, 3), Fraction(1, 2), Fraction(2, 3), Fraction(1)]}
+    n = 0
+    for kind in ("E", "A"):
+        for op, neg in ((">=", "<"), (">", "<=")):
+            for c in consts[kind]:
+                for v in _count_vectors(5):
+                    b = counting.valuate(counting_quant(kind, op, c), list(v))
+                    d = counting.valuate(counting_quant(kind, neg, c), list(v))
+                    assert d == 5 - b, (kind, op, c, v, b, d)
+                    n += 1
+    assert n > 5000
+
+
+def test_negated_constraint_gives_dual_verdict():
+    _check_negation_duality()
+
+
 # ------------------------------------------------------------------ planted mistakes
 def _weak_next(f, letters, ap_truth, memo=None):
     if f[0] == "X":
@@ -209,3 +231,21 @@ def test_ladder_wrong_index_caught_by_monotonicity(monkeypatch):
     monkeypatch.setattr(counting, "_ladder", wrong_index)
     with pytest.raises(AssertionError):
         _check_ladder_monotone()
+
+
+def test_ladder_wrong_sum_caught_by_duality(monkeypatch):
+    # a '<=' ladder whose Tc rung also leaves out the Fp children must break
+    # the duality with '>'
+    orig = counting._ladder
+
+    def wrong_sum(kind, op, const, v):
+        b = orig(kind, op, const, v)
+        if op not in ("<=", "<") or b in (T, counting.TC):
+            return b
+        N = sum(v)
+        if counting.constraint(kind, op, const, N - v[F] - v[counting.FC] - v[counting.FP], N):
+            return counting.TC
+        return b
+    monkeypatch.setattr(counting, "_ladder", wrong_sum)
+    with pytest.raises(AssertionError):
+        _check_negation_duality()
