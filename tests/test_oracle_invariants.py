@@ -155,6 +155,26 @@ def test_negated_constraint_gives_dual_verdict():
     _check_negation_duality()
 
 
+def test_negated_outer_constraint_on_traces():
+    # the same through the whole trace -> verdict function: negating the
+    # outermost constraint gives the dual root verdict and changes nothing below
+    rng = np.random.default_rng(14)
+    neg = {">=": "<", "<": ">=", ">": "<=", "<=": ">"}
+    outer = [("A", "0.5"), ("A", "0.25"), ("A", "1"), ("A", "0"), ("E", "2"), ("E", "0"), ("E", "1")]
+    for _ in range(80):
+        kind, c = outer[rng.integers(len(outer))]
+        op = list(neg)[rng.integers(4)]
+        body = BODIES[rng.integers(len(BODIES))]
+        nested = bool(rng.integers(2))
+        inner = f"{QUANTS[rng.integers(len(QUANTS))]} y: q(x,y) => " if nested else ""
+        keys, preds = _trace(rng, int(rng.integers(1, 40)), 2 if nested else 1)
+        fa = f"{kind}_{{{op}{c}}} x: p(x) => {inner}{body}"
+        fb = f"{kind}_{{{neg[op]}{c}}} x: p(x) => {inner}{body}"
+        ra, rb = verify(fa, SCH, keys, preds), verify(fb, SCH, keys, preds)
+        assert rb.root == 5 - ra.root, (fa, ra.root, rb.root)
+        assert ra.root_counts == rb.root_counts and ra.verdicts == rb.verdicts
+
+
 # ------------------------------------------------------------------ planted mistakes
 def _weak_next(f, letters, ap_truth, memo=None):
     if f[0] == "X":
