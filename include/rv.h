@@ -88,9 +88,14 @@ typedef struct {
   int alphabet;
 } rv_formula_info;
 
-/* Parse `text` (Def. 1 syntax, defaults A = A_{=1}, E = E_{>=1}; see the
- * DESIGN notes for the concrete grammar) and synthesise the LTL4 monitor of
- * its body over the schema's alphabet (Def. "LTL4 Monitor", Sec. 2.2.3).
+/* Parse `text` (Def. 1 syntax, defaults A = A_{=1}, E = E_{>=1}) and
+ * synthesise the LTL4 monitor of its body over the schema's alphabet
+ * (Def. "LTL4 Monitor", Sec. 2.2.3).  Concrete grammar: a formula is zero to
+ * two binders `Q_{~c} x: p(x) =>` followed by the body; Q is A (c a decimal
+ * or percentage in [0,1]) or E (c an integer >= 0), ~ one of < <= > >= =;
+ * the body is LTL over the schema's code names with ! && || -> <-> (also
+ * & | and =>), X F G, and infix U R W, tightest first: unary operators,
+ * U/R/W, &&, ||, ->, <->.
  * On error returns RV_EPARSE / RV_EUNSUPPORTED / RV_EINVAL and writes a
  * message into err[errlen] (may be NULL).  *out is owned by the caller and
  * released with rv_formula_free.  Host only; no GPU work. */
@@ -108,8 +113,13 @@ rv_status rv_formula_quantifier(const rv_formula* f, int level, int* kind, int* 
 void rv_formula_free(rv_formula* f);
 
 /* Six-valued valuation of one quantifier node from its child-verdict counts
- * v[0..5] (Eq. S and Def. "LTL4-C Semantics"; readings in the DESIGN notes).
- * Host entry of the same function the reduce kernels run. */
+ * v[0..5] (Eq. S and Def. "LTL4-C Semantics").  The cases are tried
+ * top-down in lattice order; for >=/> the count sums are the printed ones,
+ * for <=/< the mirrored ones (the children that could still be true push the
+ * count up), '=' is an exact integer equality under the same rungs, and the
+ * permanence rules are Table 1 (E) and, for A, what holds for every
+ * continuation that adds children of any verdict.  Host entry of the same
+ * function the reduce kernels run. */
 rv_status rv_valuate(int kind, int op, uint64_t num, uint64_t den, const uint64_t v[6], int* verdict);
 
 /* ------------------------------------------------------------------ offline verification */

@@ -11,7 +11,7 @@ children, and a set B of truth values with n = sum of v[b] over b in B,
 Def. "LTL4-C Semantics" assigns one of the six values from such constraints
 plus permanence conditions.  The definition as printed is garbled in places,
 so this module fixes one reading and every other part of the project follows
-it (the same list of readings is kept in the design notes):
+it:
 
  * cases are tried top-down in lattice order and the first one that applies
    wins (Sec. 2.3: Tp only when Tc fails, Fp only when Tp and Tc fail);
@@ -26,7 +26,13 @@ it (the same list of readings is kept in the design notes):
    Tp if (v[T]+v[Tc]+v[Tp]) ~, Fp if (v[T]+v[Tc]) ~, F if permanently violated,
    else Fc (this makes Table 1's direction hold: E_{<=c} is violated for good
    once more than c children are definitely true);
- * ~ is '=' : the meet (minimum) of the '>=' and '<=' verdicts;
+ * ~ is '=' : the same rungs with Eq. S an exact equality n*q = p*N:
+   Tc if both v[T]+v[Tc] and v[T]+v[Tc]+v[Tp]+v[Fp] meet it (so does every
+   count between), Tp if v[T]+v[Tc]+v[Tp] meets it, Fp if some count of true
+   children between those two meets it, F if permanently violated (E: v[T] > l,
+   Table 1; A: c = 1 and v[F] >= 1, or c = 0 and v[T] >= 1), else Fc; never T,
+   since a continuation can always add a child that breaks the equality.  This
+   gives E_{=0} = E_{<=0} (case study 3) and A_{=1} = A_{>=1} (Sec. 2.4.5);
  * permanence: the E rules of Table 1 (>, >=: permanently satisfied once the
    constraint holds on v[T]; =, <, <=: permanently violated once it fails on
    v[T]) and, for A with c = p/q, the rules obtained by letting a
@@ -38,11 +44,13 @@ it (the same list of readings is kept in the design notes):
    (one F child makes it F), which this reproduces.
  * N = 0 (a root with no bindings) is decided by the same integer comparisons.
 
-Parity unpinned: these readings beyond the worked example, Table 1, the
-A_{=1} rule and the case-study thresholds have no values in the paper to be
-checked against; the tests only hold them to the order of B6 (moving a child
-up the chain never lowers a '>=' or '>' node, nor raises a '<=' or '<' one)
-and to negation (a negated constraint gives the dual verdict).
+Pins: beyond the worked example, Table 1, the A_{=1} rule and the
+case-study thresholds, every rung and permanence rule here is checked against
+an enumeration of how a node's children can still turn out (a T or F child
+keeps its value, any other child may end either way, a continuation may add
+children of any verdict; tests/test_oracle_permanence.py), for every count
+vector with at most six children, every comparison and several constants, and
+held to the order of B6 and to negation by the invariant tests.
 """
 from __future__ import annotations
 
@@ -125,10 +133,28 @@ def _ladder(kind, op, const, v):
     return FC
 
 
+def _equality(kind, const, v):
+    N = sum(v)
+    lo = v[T] + v[TC]                 # presumptive children all false
+    hi = lo + v[TP] + v[FP]           # presumptive children all true
+    C = lambda n: constraint(kind, "=", const, n, N)  # noqa: E731
+    if C(lo) and C(hi):
+        return TC
+    if C(lo + v[TP]):
+        return TP
+    if any(C(n) for n in range(lo, hi + 1)):
+        return FP
+    if kind == "E":
+        viol = v[T] > int(const)
+    else:
+        viol = (const == 1 and v[F] >= 1) or (const == 0 and v[T] >= 1)
+    return F if viol else FC
+
+
 def valuate(q, v) -> int:
     """Six-valued verdict of a quantifier node with child-verdict counts v[0..5]."""
     if len(v) != 6:
         raise ValueError("v must have six entries")
     if q.op == "=":
-        return min(_ladder(q.kind, ">=", q.const, v), _ladder(q.kind, "<=", q.const, v))
+        return _equality(q.kind, q.const, v)
     return _ladder(q.kind, q.op, q.const, v)

@@ -12,7 +12,11 @@
 //                  F  if permanently violated, else Fc
 //   ~ in {<=, <}:  the same cascade on the mirrored counts
 //                  N - v_F, N - v_F - v_Fc, v_T + v_Tc + v_Tp, v_T + v_Tc
-//   ~ is '=':      the minimum of the '>=' and '<=' verdicts.
+//   ~ is '=':      the same rungs with the constraint an exact equality:
+//                  Tc if C(v_T + v_Tc) and C(v_T + v_Tc + v_Tp + v_Fp),
+//                  Tp if C(v_T + v_Tc + v_Tp), Fp if some count between the
+//                  first two meets it, F if permanently violated, else Fc
+//                  (never T: a continuation can always break an equality).
 // Permanence: E follows Table 1 (>, >=: satisfied for good once C(v_T);
 // =, <=, <: violated for good once !C(v_T)).  A with c = num/den:
 //   >=: sat iff c = 0, viol iff c = 1 and v_F >= 1
@@ -95,11 +99,25 @@ RV_HD int ladder(int kind, int op, uint64_t num, uint64_t den, const uint64_t* v
   return VFC;
 }
 
-RV_HD int valuate(int kind, int op, uint64_t num, uint64_t den, const uint64_t* v) {
-  if (op == EQ) {
-    int a = ladder(kind, GE, num, den, v), b = ladder(kind, LE, num, den, v);
-    return a < b ? a : b;
+RV_HD int equality(int kind, uint64_t num, uint64_t den, const uint64_t* v) {
+  const uint64_t N = v[0] + v[1] + v[2] + v[3] + v[4] + v[5];
+  const uint64_t lo = v[VT] + v[VTC], hi = lo + v[VTP] + v[VFP];
+  if (constraint(kind, EQ, num, den, lo, N) && constraint(kind, EQ, num, den, hi, N)) return VTC;
+  if (constraint(kind, EQ, num, den, lo + v[VTP], N)) return VTP;
+  // is there an integer count n in [lo, hi] with n == l (E) or n * den == num * N (A)?
+  if (kind == QE) {
+    if (num >= lo && num <= hi) return VFP;
+  } else {
+    const u128 t = (u128)num * N;
+    if (t % den == 0 && t / den >= lo && t / den <= hi) return VFP;
   }
+  const bool viol = kind == QE ? v[VT] > num
+                               : ((num == den && v[VF] >= 1) || (num == 0 && v[VT] >= 1));
+  return viol ? VF : VFC;
+}
+
+RV_HD int valuate(int kind, int op, uint64_t num, uint64_t den, const uint64_t* v) {
+  if (op == EQ) return equality(kind, num, den, v);
   return ladder(kind, op, num, den, v);
 }
 

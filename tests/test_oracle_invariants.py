@@ -209,8 +209,9 @@ _orig_progress = ltl4.progress
 @pytest.mark.parametrize("target,attr,fake,checks", [
     (fltl, "evaluate", _weak_next, [pins.test_fltl_closed_forms]),
     (counting, "constraint", _swap_sign, [pins.test_table1_exhaustive, pins.test_case_study1_threshold]),
-    (counting, "permanently_violated", lambda *a: False,
-     [pins.test_worked_example, pins.test_A_eq_1_single_violation]),
+    (counting, "permanently_violated", lambda *a: False, [pins.test_worked_example]),
+    (counting, "_equality", lambda kind, const, v: counting.FC if v[F] else counting.TC,
+     [pins.test_A_eq_1_single_violation]),
     (ltl4, "progress", _progress_drops_until_now, [pins.test_ltl4_fig1_monitor_shape]),
 ])
 def test_pins_catch_planted_mistakes(monkeypatch, target, attr, fake, checks):
