@@ -181,7 +181,13 @@ rv_status rv_verify_trace(const rv_formula* f, const rv_trace* t, int on_device,
 
 /* Asynchronous form for device-resident traces: enqueues all work on s and
  * writes the result into the device struct *dev_out; no host synchronisation.
- * The caller reads dev_out after synchronising s. */
+ * The caller reads dev_out after synchronising s.  Device-side outcomes are in
+ * dev_out->status: RV_EINVAL for a bad trace (predicate code out of range,
+ * timestamps decreasing); RV_EAGAIN, for two-quantifier formulas only, when
+ * more distinct outer values fell into one key bucket than a fold unit can
+ * count (256; the default split uses 2^15 buckets by hash of the outer value,
+ * so only keys crafted to collide reach it) -- rerun through rv_verify_trace,
+ * which reports it as an error with a message. */
 rv_status rv_verify_trace_async(const rv_formula* f, const rv_trace* t, void* ws, size_t ws_bytes,
                                 rv_result* dev_out, const rv_bindings* bindings,
                                 const rv_verify_opts* opts, cudaStream_t s);
@@ -294,11 +300,17 @@ uint64_t rv_launch_count(void);
  * loads librv keeps until the process exits.
  * Limits: traces of at most 1,000,000 events (and whose workspace fits the
  * 64 MiB); longer ones return RV_EINVAL with a message, nothing is queued.
+ * Device-side outcomes are in dev_out->status exactly as for
+ * rv_verify_trace_async (RV_EAGAIN there: outer values crafted to collide in
+ * one key bucket; rerun through rv_verify_trace with a workspace).
  * The first call on a device looks up the array's device address (set-up,
- * once per device, with that device current); make that first call before
- * any stream capture.  All calls share the one array and each call clears
- * what must start at zero: calls whose work overlaps on the GPU (different
- * streams, or host threads without ordering) race and give wrong results. */
+ * once per device, with that device current) and keeps it for the life of
+ * the process; make that first call before any stream capture.  A
+ * cudaDeviceReset of that device invalidates the kept address: do not call
+ * this entry point on a device after resetting it in the same process.  All
+ * calls share the one array and each call clears what must start at zero:
+ * calls whose work overlaps on the GPU (different streams, or host threads
+ * without ordering) race and give wrong results. */
 rv_status rv_verify_trace_noalloc(const rv_formula* f, const rv_trace* t, rv_result* dev_out, cudaStream_t s);
 
 /* Last error message of the calling thread (never NULL). */

@@ -39,9 +39,10 @@ def stale() -> bool:
 def build(force: bool = False, verbose: bool = False) -> str:
     if not force and not stale():
         return LIB
-    objs = []
+    from concurrent.futures import ThreadPoolExecutor
     tmpdir = os.path.join(HERE, "_build")
     os.makedirs(tmpdir, exist_ok=True)
+    cmds = []
     for src in sources():
         obj = os.path.join(tmpdir, os.path.basename(src) + ".o")
         cmd = [_nvcc(), "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC",
@@ -50,8 +51,13 @@ def build(force: bool = False, verbose: bool = False) -> str:
             cmd[1:1] = ["-x", "cu"]
         if verbose:
             print(" ".join(cmd))
-        subprocess.run(cmd, check=True)
-        objs.append(obj)
+        cmds.append((cmd, obj))
+    # translation units compile independently: one nvcc per source
+    with ThreadPoolExecutor(max_workers=max(1, min(len(cmds), os.cpu_count() or 1))) as ex:
+        for r in list(ex.map(lambda c: subprocess.run(c[0]), cmds)):
+            if r.returncode:
+                raise subprocess.CalledProcessError(r.returncode, r.args)
+    objs = [obj for _, obj in cmds]
     cmd = [_nvcc(), "-shared", *ARCH, "-o", LIB, *objs, "-lcuda"]
     if verbose:
         print(" ".join(cmd))

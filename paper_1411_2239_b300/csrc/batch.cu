@@ -583,15 +583,7 @@ rv_status build_plan(rv_batch* b) {
   return RV_OK;
 }
 
-int num_sms_b() {
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-      sms = 148;
-  }
-  return sms;
-}
+int num_sms_b() { return rv_num_sms(); }
 
 rv_status enqueue(rv_batch* b, const uint32_t* key, const uint8_t* pred, unsigned char* ws, rv_result* res,
                   cudaStream_t s) {
@@ -678,7 +670,11 @@ extern "C" size_t rv_batch_workspace_size(const rv_batch* b) {
   return worst;
 }
 
-static bool g_bfold_attr = false;
+// the attribute applies to the current device: set it once per device
+static rv_status set_bfold_attr() {
+  BCU(cudaFuncSetAttribute(k_bfold, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BFoldShared)));
+  return RV_OK;
+}
 
 extern "C" rv_status rv_batch_run(rv_batch* b, const uint32_t* key, const uint8_t* pred, void* ws, size_t ws_bytes,
                                   rv_result* dev_results, cudaStream_t s) {
@@ -686,10 +682,7 @@ extern "C" rv_status rv_batch_run(rv_batch* b, const uint32_t* key, const uint8_
     return rv_fail(RV_EINVAL, "null argument");
   const BatchLayout L = layout(b, b->dev.NB, b->hist_entries);
   if (ws_bytes < L.total) return rv_fail(RV_ENOMEM, "workspace of %zu bytes, need %zu", ws_bytes, L.total);
-  if (!g_bfold_attr) {
-    BCU(cudaFuncSetAttribute(k_bfold, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BFoldShared)));
-    g_bfold_attr = true;
-  }
+  if (rv_status st = rv_once_per_device(RV_ONCE_BATCH, &set_bfold_attr)) return st;
   if (rv_prof_enabled())   // per-kernel events need eager launches, not a graph replay
     return enqueue(b, key, pred, (unsigned char*)ws, dev_results, s);
   if (!b->exec || b->g_key != key || b->g_pred != pred || b->g_ws != ws || b->g_res != dev_results) {

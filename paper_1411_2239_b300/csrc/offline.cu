@@ -2042,15 +2042,7 @@ struct Plan {
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-static int num_sms() {
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-      sms = 148;
-  }
-  return sms;
-}
+static int num_sms() { return rv_num_sms(); }
 
 static Plan make_plan(const rv_formula* f, uint64_t n, int host_input, const rv_verify_opts* o, int extra_b2,
                       bool stream = false) {
@@ -2062,8 +2054,13 @@ static Plan make_plan(const rv_formula* f, uint64_t n, int host_input, const rv_
   int b1 = o && o->bucket_bits ? o->bucket_bits : 8;
   pl.B1 = std::min(11, std::max(8, b1));
   pl.P1 = 1 << pl.B1;
+  // two variables: the finest split by default, because a fold unit counts
+  // the outer bindings of its bucket in a table of UCAP entries, and only the
+  // finest split keeps the outer values of any natural trace below that
+  // (more than UCAP distinct outer values would have to share 15 hash bits)
   int b2 = 0;
   if (o && o->sub_bucket_bits) b2 = o->sub_bucket_bits;
+  else if (pl.F == FMT_K2) b2 = 7;
   else while (b2 < 7 && (n >> (pl.B1 + b2)) > 8192) ++b2;
   b2 += extra_b2;
   pl.B2 = std::min(7, std::max(0, b2));
@@ -2291,11 +2288,8 @@ static rv_status launch_all(const Plan& pl, const rv_formula* f, const void* key
   return RV_OK;
 }
 
-static bool g_attr_done[3];
-
 template <int F>
-static rv_status set_attrs() {
-  if (g_attr_done[F]) return RV_OK;
+static rv_status set_attrs_now() {
   RV_CU(cudaFuncSetAttribute(k_fold<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(FoldShared<F>)));
   RV_CU(cudaFuncSetAttribute(k_combine<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(CombineShared)));
   RV_CU(cudaFuncSetAttribute(k_hist<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, SC_WARPS * 2048 * 4));
@@ -2304,8 +2298,14 @@ static rv_status set_attrs() {
   RV_CU(cudaFuncSetAttribute(k_scan<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)scan_smem<uint32_t>()));
   RV_CU(cudaFuncSetAttribute(k_scan<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)scan_smem<uint64_t>()));
   RV_CU(cudaFuncSetAttribute(k_scatter2_tile<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Tile2Shared<F>)));
-  g_attr_done[F] = true;
   return RV_OK;
+}
+
+// the attributes apply to the current device: set them once per device
+template <int F>
+static rv_status set_attrs() {
+  return rv_once_per_device(F == FMT_K32 ? RV_ONCE_FOLD32 : F == FMT_K64 ? RV_ONCE_FOLD64 : RV_ONCE_FOLD2,
+                            &set_attrs_now<F>);
 }
 
 static rv_status dispatch(const Plan& pl, const rv_formula* f, const void* key, const uint8_t* pred, const uint32_t* ts,

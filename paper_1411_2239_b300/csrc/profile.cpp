@@ -80,3 +80,34 @@ extern "C" int rv_profile_collect(rv_kernel_stat* out, int max) {
   g_stats.clear();
   return n;
 }
+
+namespace {
+std::mutex g_once_mu;
+bool g_once_done[RV_MAX_DEVICES][RV_ONCE_SLOTS];
+int g_sms[RV_MAX_DEVICES];
+}  // namespace
+
+rv_status rv_once_per_device(int slot, rv_status (*fn)()) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return rv_fail(RV_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+  if (dev < 0 || dev >= RV_MAX_DEVICES || slot < 0 || slot >= RV_ONCE_SLOTS)
+    return rv_fail(RV_EINVAL, "device %d beyond the %d the library supports", dev, RV_MAX_DEVICES);
+  std::lock_guard<std::mutex> lk(g_once_mu);
+  if (g_once_done[dev][slot]) return RV_OK;
+  rv_status st = fn();
+  if (st == RV_OK) g_once_done[dev][slot] = true;
+  return st;
+}
+
+int rv_num_sms() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= RV_MAX_DEVICES) return 148;
+  std::lock_guard<std::mutex> lk(g_once_mu);
+  if (!g_sms[dev]) {
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) return 148;
+    g_sms[dev] = sms;
+  }
+  return g_sms[dev];
+}

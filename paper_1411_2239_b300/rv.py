@@ -194,9 +194,11 @@ def workspace_size(formula: Formula, n: int, host_input: bool = False, opts=None
 _ws_cache = {}
 
 
-def workspace(nbytes: int, device="cuda"):
-    """A cached torch uint8 device buffer of at least nbytes."""
+def workspace(nbytes: int, device=None):
+    """A cached torch uint8 buffer of at least nbytes on the current device."""
     import torch
+    if device is None:
+        device = torch.device("cuda", torch.cuda.current_device())
     buf = _ws_cache.get(device)
     if buf is None or buf.numel() < nbytes:
         _ws_cache.pop(device, None)

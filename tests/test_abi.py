@@ -161,3 +161,15 @@ def test_binding_structs_mirror_the_header():
     for cname, cls in pairs.items():
         assert cname in hs, cname
         assert [f[0] for f in cls._fields_] == hs[cname], (cname, hs[cname])
+
+
+def test_noalloc_scratch_covers_a_million_events_in_every_key_format(rv):
+    # the no-allocation entry point's fixed scratch array is 64 MiB and it
+    # accepts traces of up to 1,000,000 events: the workspace of such a trace
+    # must fit for one 32-bit key, one 64-bit key and two variables
+    cases = [("A_{>=0.95} s: socket(s) => G(receive -> F respond)", synth.SOCKET_CODES, 32),
+             ("A_{>=0.95} s: socket(s) => G(receive -> F respond)", synth.SOCKET_CODES, 64),
+             ("A_{>=0.90} u: user(u) => E_{<=3} f: file(u,f) => open && !F close", synth.FILE_CODES, 64)]
+    for text, codes, bits in cases:
+        f = rv.Formula(text, codes, key_bits=bits)
+        assert rv.workspace_size(f, 1_000_000) <= 64 << 20, (text, bits)

@@ -282,3 +282,15 @@ def test_level2_scan_in_slices(rv, torch_cuda):
     pred = rng.integers(0, 3, size=len(key)).astype(np.uint8)
     for opts in [{"sub_bucket_bits": 3}, {"sub_bucket_bits": 3, "no_heavy": 1}]:
         _check(rv, torch_cuda, C1, synth.SOCKET_CODES, key, pred, opts=opts)
+
+
+def test_two_devices_in_one_process(rv, torch_cuda):
+    # kernel attributes (dynamic shared-memory limits) belong to the device
+    # that is current when they are set: the offline path must configure each
+    # device it runs on, not only the first
+    if torch_cuda.cuda.device_count() < 2:
+        pytest.skip("needs two visible GPUs")
+    tr = synth.socket_trace(200_000, 5_000, pending_frac=0.03, zipf_s=1.1, seed=31)
+    for d in (0, 1, 0):
+        with torch_cuda.cuda.device(d):
+            _check(rv, torch_cuda, C1, tr.codes, tr.key, tr.pred)

@@ -75,6 +75,91 @@ def test_noalloc_matches_workspace_entry_on_consecutive_calls():
         assert _same(got, want), (got, want)
 
 
+def test_noalloc_two_variables_at_the_event_limit():
+    # exactly 1,000,000 events of the nested workload's shape: the largest
+    # trace the entry point accepts, in the key format with the largest plan
+    import torch
+    t = synth.file_trace(1_000_000, 2_000, 50_000, seed=4)
+    t.key, t.pred = t.key[:1_000_000], t.pred[:1_000_000]
+    assert len(t.pred) == 1_000_000
+    f = rv.Formula(C3, t.codes, key_bits=64)
+    key, pred = _dev(torch, t.key), _dev(torch, t.pred)
+    for _ in range(2):
+        st, got = _noalloc(torch, f, key, pred)
+        assert st == rv.RV_OK, rv.last_error()
+        want = _reference(torch, f, key, pred)
+        assert want.status == 0 and _same(got, want), (got, want)
+
+
+def _fmix32(x):
+    """MurmurHash3's 32-bit finaliser (public domain): the library takes a
+    two-variable key's bucket from the top bits of this mix of the outer value."""
+    x = x.astype(np.uint64)
+    x ^= x >> np.uint64(16)
+    x = (x * np.uint64(0x85EBCA6B)) & np.uint64(0xFFFFFFFF)
+    x ^= x >> np.uint64(13)
+    x = (x * np.uint64(0xC2B2AE35)) & np.uint64(0xFFFFFFFF)
+    x ^= x >> np.uint64(16)
+    return x.astype(np.uint32)
+
+
+def _users_sharing(top_bits, count, seed):
+    rng = np.random.default_rng(seed)
+    cand = np.unique(rng.integers(1, 2**32, size=20_000_000, dtype=np.uint64).astype(np.uint32))
+    top = _fmix32(cand) >> np.uint32(32 - top_bits)
+    vals, counts = np.unique(top, return_counts=True)
+    users = cand[top == vals[np.argmax(counts)]][:count]
+    assert len(users) == count
+    return users
+
+
+def _nested_trace(users, files_per_user, seed):
+    # per (user, file): open, read, then close unless it is the user's last
+    # file (one leaked file per user, so the inner E_{<=3} stays satisfied);
+    # the pairs are interleaved at random times, each keeping its own order
+    rng = np.random.default_rng(seed)
+    keys, preds, times = [], [], []
+    for u in users:
+        for f in range(files_per_user):
+            k = (int(u) << 32) | (f + 1)
+            seq = [0, 2] + ([1] if f + 1 < files_per_user else [])
+            keys += [k] * len(seq)
+            preds += seq
+            times += sorted(rng.random(len(seq)).tolist())
+    order = np.argsort(np.array(times), kind="stable")
+    return np.array(keys, dtype=np.uint64)[order], np.array(preds, dtype=np.uint8)[order]
+
+
+def test_noalloc_many_outer_values_in_one_first_level_bucket():
+    # 400 users whose hashes share the 8 bits of the first-level split: more
+    # outer values than a fold unit counts (256) unless the second-level split
+    # separates them, which the default plan for two variables does
+    import torch
+    from oracle.verify import Schema, verify
+    users = _users_sharing(8, 400, seed=5)
+    k, p = _nested_trace(users, 3, seed=6)
+    f = rv.Formula(C3, synth.FILE_CODES, key_bits=64)
+    key, pred = _dev(torch, k), _dev(torch, p)
+    st, got = _noalloc(torch, f, key, pred)
+    assert st == rv.RV_OK, rv.last_error()
+    o = verify(C3, Schema(synth.FILE_CODES), k, p)
+    assert got.status == rv.RV_OK
+    assert (got.root, got.root_counts, got.level_counts) == (o.root, o.root_counts, o.level_counts)
+
+
+def test_noalloc_reports_outer_values_crafted_to_collide():
+    # 300 users whose hashes share all 15 bits of the finest split land in one
+    # key bucket: the call is accepted and queued, and the device result says
+    # RV_EAGAIN (more outer values than a fold unit counts), as documented
+    import torch
+    users = _users_sharing(15, 300, seed=7)
+    k, p = _nested_trace(users, 2, seed=8)
+    f = rv.Formula(C3, synth.FILE_CODES, key_bits=64)
+    st, got = _noalloc(torch, f, _dev(torch, k), _dev(torch, p))
+    assert st == rv.RV_OK, rv.last_error()
+    assert got.status == rv.RV_EAGAIN
+
+
 def test_noalloc_rejects_traces_over_the_limit():
     import torch
     f = rv.Formula(C1, synth.SOCKET_CODES)
