@@ -192,6 +192,40 @@ rv_status rv_verify_trace_async(const rv_formula* f, const rv_trace* t, void* ws
                                 rv_result* dev_out, const rv_bindings* bindings,
                                 const rv_verify_opts* opts, cudaStream_t s);
 
+/* ------------------------------------------------------------------ one trace over several ranks
+ * Algorithm 1 (Sec. 4.2) evaluates every binding on its own projection
+ * (Sec. 2.4.3); all bindings of one outer value d_0 form one subtree of the
+ * submonitor tree (Sec. 3.3), and the only step that joins subtrees,
+ * ApplyQuantifiers, counts verdicts per level (the vectors v of Sec. 3.4),
+ * which are sums.  So a trace splits by its outermost quantified value into
+ * parts that are verified independently (one per rank), and the parts' counts
+ * add up to the whole trace's.  Rank of an event: a hash of its outer value
+ * (the key with one variable, key >> 32 with two) scaled to [0, world); it is
+ * independent of the key mixing inside the verifier.
+ *   rv_shard_of: the rank of each of n host keys (key_bits of f), written to
+ *     the host array rank_out[n].  Host only; no GPU work.
+ *   rv_shard_workspace_size / rv_shard_trace: device form.  t holds device
+ *     arrays; the events are written to key_out/pred_out (and ts_out when t
+ *     has timestamps), device arrays of n entries, grouped into world
+ *     contiguous segments in rank order, trace order kept inside every
+ *     segment; counts_out (device uint64[world]) receives the segment sizes.
+ *     ws: device workspace of at least rv_shard_workspace_size bytes.  Work is
+ *     queued on s; nothing is synchronised.  1 <= world <= 256.
+ *   rv_combine_results: the result of the whole trace from the results of its
+ *     parts (host structs): counts, node numbers and events summed, the root
+ *     valuated on the summed root counts, the first failed part's status.  A
+ *     single part that already holds summed counts (an all-reduce) is
+ *     re-valuated the same way.
+ * Errors: RV_EINVAL (null arguments, world out of range, an unquantified
+ * property -- its one binding is the whole trace -- with world > 1),
+ * RV_ENOMEM (workspace), RV_ECUDA. */
+rv_status rv_shard_of(const rv_formula* f, const void* key, uint64_t n, int world, uint32_t* rank_out);
+size_t rv_shard_workspace_size(uint64_t n, int world);
+rv_status rv_shard_trace(const rv_formula* f, const rv_trace* t, int world, void* ws, size_t ws_bytes,
+                         void* key_out, uint8_t* pred_out, uint32_t* ts_out, uint64_t* counts_out,
+                         cudaStream_t s);
+rv_status rv_combine_results(const rv_formula* f, const rv_result* parts, int n_parts, rv_result* out);
+
 /* ------------------------------------------------------------------ batched verification
  * Many traces of uneven length, each checked against its own list of nf
  * single-quantifier formulas (nf <= 32), in one fixed sequence of launches

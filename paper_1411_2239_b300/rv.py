@@ -282,6 +282,69 @@ def parse_result(raw: bytes) -> Result:
     return _result(r)
 
 
+# ---------------------------------------------------------------------- one trace over several ranks
+def _shard_sigs(L):
+    if getattr(L, "_shard_sigs", False):
+        return
+    vp, u64 = ctypes.c_void_p, ctypes.c_uint64
+    L.rv_shard_of.argtypes = [vp, vp, u64, ctypes.c_int, vp]
+    L.rv_shard_workspace_size.argtypes = [u64, ctypes.c_int]
+    L.rv_shard_workspace_size.restype = ctypes.c_size_t
+    L.rv_shard_trace.argtypes = [vp, ctypes.POINTER(_Trace), ctypes.c_int, vp, ctypes.c_size_t, vp, vp, vp, vp, vp]
+    L.rv_combine_results.argtypes = [vp, ctypes.POINTER(_Result), ctypes.c_int, ctypes.POINTER(_Result)]
+    L._shard_sigs = True
+
+
+def shard_of(formula: Formula, key, world: int) -> np.ndarray:
+    """Rank in [0, world) of every event of a host key array (rv_shard_of)."""
+    L = lib()
+    _shard_sigs(L)
+    key = np.ascontiguousarray(key, dtype=np.uint64 if formula.key_bits == 64 else np.uint32)
+    out = np.empty(len(key), dtype=np.uint32)
+    _check(L.rv_shard_of(formula.handle, key.ctypes.data, len(key), world, out.ctypes.data))
+    return out
+
+
+def shard_trace(formula: Formula, key, pred, world: int, ts=None, stream=None):
+    """Group a device trace into world contiguous segments by rank (rv_shard_trace).
+    Returns (key_out, pred_out, ts_out or None, counts) with counts a device
+    uint64 tensor (as int64) of the segment sizes."""
+    import torch
+    L = lib()
+    _shard_sigs(L)
+    n = int(pred.shape[0])
+    key_out = torch.empty_like(key)
+    pred_out = torch.empty_like(pred)
+    ts_out = None if ts is None else torch.empty_like(ts)
+    counts = torch.empty(world, dtype=torch.int64, device=pred.device)
+    ws = workspace(int(L.rv_shard_workspace_size(n, world)))
+    tr = _Trace(_ptr(key), _ptr(pred), _ptr(ts), n)
+    _check(L.rv_shard_trace(formula.handle, ctypes.byref(tr), world, ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                            _ptr(key_out), _ptr(pred_out), _ptr(ts_out), _ptr(counts), _stream_handle(stream)))
+    return key_out, pred_out, ts_out, counts
+
+
+def _to_c(r: Result) -> _Result:
+    c = _Result()
+    c.root, c.status, c.events = r.root, r.status, r.events
+    for v in range(6):
+        c.root_counts[v] = r.root_counts[v]
+        c.level_counts[0][v] = r.level_counts[0][v]
+        c.level_counts[1][v] = r.level_counts[1][v]
+    c.n_nodes[0], c.n_nodes[1] = r.n_nodes
+    return c
+
+
+def combine_results(formula: Formula, parts) -> Result:
+    """The whole trace's result from its parts' results (rv_combine_results)."""
+    L = lib()
+    _shard_sigs(L)
+    arr = (_Result * len(parts))(*[_to_c(p) for p in parts])
+    out = _Result()
+    _check(L.rv_combine_results(formula.handle, arr, len(parts), ctypes.byref(out)))
+    return _result(out)
+
+
 # ---------------------------------------------------------------------- batched
 class _BatchOpts(ctypes.Structure):
     _fields_ = [("bucket_records", ctypes.c_int), ("tile_events", ctypes.c_int)]
