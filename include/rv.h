@@ -263,7 +263,7 @@ void rv_batch_free(rv_batch* b);
  * arrived events update the submonitor tree, whose state stays on the GPU.
  * A service owns one formula (one or two quantifiers; one-quantifier streams
  * use 32-bit keys, two-quantifier streams 64-bit (d0 << 32) | d1 keys) and up
- * to max_streams streams, each an independent trace.  Continuous batching: a
+ * to max_streams open streams, each an independent trace.  Continuous batching: a
  * push only stages the chunk (host copy) and returns; a worker thread batches
  * every staged chunk (at most one per stream per batch) onto the GPU while
  * newer chunks keep arriving.  Every processed chunk yields one
@@ -275,7 +275,18 @@ void rv_batch_free(rv_batch* b);
  *     max_outer); retry later.  RV_EINVAL: closed stream, decreasing ts.
  *   rv_stream_poll: up to max verdicts in ticket order; waits up to
  *     timeout_us; RV_ETIMEOUT when none arrived.
- *   rv_stream_close: drops the stream's queued chunks and verdicts.
+ *   rv_stream_close: drops the stream's queued chunks and verdicts and ends
+ *     the handle (no call may use it afterwards).  Once no batch on the GPU
+ *     carries its chunks, its bindings and outer nodes are retired on the
+ *     device (their table entries and ids are reused by later bindings, so
+ *     their memory counts toward admission again) and its slot is given back
+ *     to rv_stream_open.
+ *   Batches overlap: the worker stages and copies batch k+1 (its own pinned
+ *   and device buffers, a copy stream) while batch k's kernels run; kernels
+ *   run in batch order on one stream, so every chunk's verdict is that of its
+ *   stream's prefix.  A batch that fails on the device gives its chunks that
+ *   status and fails only the streams it carried (their later pushes return
+ *   RV_EINVAL); other streams go on.  A failed CUDA call fails the service.
  *   rv_service_close: drains the worker and frees everything (device memory
  *     through the registered allocator). */
 typedef struct rv_service rv_service;

@@ -485,17 +485,26 @@ class Service:
 
 
 class Stream:
+    """A stream of a Service.  close() ends it: the library frees the handle
+    once its queued work is retired, so a closed Stream refuses further calls."""
+
     def __init__(self, svc, h):
         self.svc, self._h = svc, h
 
+    def _handle(self):
+        if self._h is None:
+            raise RVError(RV_EINVAL, "stream is closed")
+        return self._h
+
     def push(self, key, pred, ts=None):
         """Stage a chunk (host arrays); returns its ticket; raises RVError(RV_EAGAIN) if not admitted."""
+        h = self._handle()
         key = np.ascontiguousarray(key)
         pred = np.ascontiguousarray(pred, dtype=np.uint8)
         tr = _Trace(key.ctypes.data, pred.ctypes.data, None if ts is None else np.ascontiguousarray(ts).ctypes.data,
                     len(pred))
         t = ctypes.c_uint64()
-        st = lib().rv_stream_push(self._h, ctypes.byref(tr), ctypes.byref(t))
+        st = lib().rv_stream_push(h, ctypes.byref(tr), ctypes.byref(t))
         if st != RV_OK:
             raise RVError(st, last_error())
         return t.value
@@ -503,7 +512,7 @@ class Stream:
     def poll(self, max_n=64, timeout_us=0):
         buf = (_Verdict * max_n)()
         n = ctypes.c_int()
-        st = lib().rv_stream_poll(self._h, buf, max_n, ctypes.byref(n), int(timeout_us))
+        st = lib().rv_stream_poll(self._handle(), buf, max_n, ctypes.byref(n), int(timeout_us))
         if st == RV_ETIMEOUT:
             return []
         if st != RV_OK:
@@ -512,4 +521,6 @@ class Stream:
                 for v in buf[:n.value]]
 
     def close(self):
-        lib().rv_stream_close(self._h)
+        if self._h is not None:
+            lib().rv_stream_close(self._h)
+            self._h = None

@@ -158,3 +158,98 @@ def test_close_mid_flight_keeps_other_streams(rv):
     o = oracle_verify(C1, Schema(synth.SOCKET_CODES), traces[1].key, traces[1].pred)
     assert got[0].root == o.root and got[0].root_counts == o.root_counts
     svc.close()
+
+
+def _open(rv, svc, timeout_s=30):
+    """Open a stream, waiting while every slot is still being retired."""
+    t0 = time.time()
+    while True:
+        try:
+            return svc.open_stream()
+        except rv.RVError as e:
+            if e.status != rv.RV_EAGAIN or time.time() - t0 > timeout_s:
+                raise
+            time.sleep(0.002)
+
+
+def test_slots_reused_over_open_close_cycles(rv):
+    # 200 streams opened and closed on a 64-slot service, every one with the
+    # same socket ids: a reused slot must start from an empty submonitor tree.
+    # A long-lived stream runs beside them the whole time.
+    f = rv.Formula(C1, synth.SOCKET_CODES)
+    svc = rv.Service(f, max_streams=64, max_bindings=1 << 16)
+    sch = Schema(synth.SOCKET_CODES)
+    keeper = synth.socket_trace(60_000, 500, pending_frac=0.1, seed=60)
+    kst = svc.open_stream()
+    kparts = np.array_split(np.arange(keeper.n), 50)
+    short = [synth.socket_trace(600, 40, n_pending=k % 7, seed=61 + k % 5) for k in range(200)]
+    live = []
+    for k in range(200):
+        st = _open(rv, svc)
+        _push(rv, st, short[k].key, short[k].pred)
+        live.append((st, short[k]))
+        if k % 4 == 0 and k // 4 < len(kparts):
+            _push(rv, kst, keeper.key[kparts[k // 4]], keeper.pred[kparts[k // 4]])
+        if len(live) > 40:                      # keep 40 short streams open at a time
+            st0, tr0 = live.pop(0)
+            v = _drain([st0], [1])[0]
+            o = oracle_verify(C1, sch, tr0.key, tr0.pred)
+            assert v[0].root == o.root and v[0].root_counts == o.root_counts
+            st0.close()
+    for st0, tr0 in live:
+        v = _drain([st0], [1])[0]
+        o = oracle_verify(C1, sch, tr0.key, tr0.pred)
+        assert v[0].root == o.root and v[0].root_counts == o.root_counts
+        st0.close()
+    n_k = min(50, 200 // 4)
+    got = _drain([kst], [n_k])[0]
+    end = sum(len(kparts[i]) for i in range(n_k))
+    o = oracle_verify(C1, sch, keeper.key[:end], keeper.pred[:end])
+    assert got[-1].root == o.root and got[-1].root_counts == o.root_counts
+    kst.close()
+    t0 = time.time()
+    while svc.stats()["bindings"] > 0 and time.time() - t0 < 30:   # every binding retired
+        time.sleep(0.01)
+    assert svc.stats()["bindings"] == 0
+    svc.close()
+
+
+def test_memory_readmitted_after_close(rv):
+    f = rv.Formula(C1, synth.SOCKET_CODES)
+    svc = rv.Service(f, max_bindings=2_000, max_batch_events=4_096)
+    a, b = svc.open_stream(), svc.open_stream()
+    ka = np.arange(1, 1_501, dtype=np.uint32)
+    a.push(ka, np.zeros(1_500, dtype=np.uint8))
+    assert _drain([a], [1])[0][0].status == 0
+    kb = np.arange(10_001, 11_001, dtype=np.uint32)
+    pb = np.zeros(1_000, dtype=np.uint8)
+    with pytest.raises(rv.RVError) as e:        # 1500 live + up to 1000 new > 2000
+        b.push(kb, pb)
+    assert e.value.status == rv.RV_EAGAIN
+    a.close()
+    _push(rv, b, kb, pb)                        # admitted once a's bindings are retired
+    v = _drain([b], [1])[0]
+    assert v[0].status == 0 and sum(v[0].root_counts) == 1_000
+    assert svc.stats()["bindings"] == 1_000
+    svc.close()
+
+
+def test_bad_chunk_fails_only_its_push(rv):
+    traces = [synth.socket_trace(20_000, 200, pending_frac=0.1, seed=70 + i) for i in range(3)]
+    f = rv.Formula(C1, synth.SOCKET_CODES)
+    svc = rv.Service(f)
+    sts = [svc.open_stream() for _ in traces]
+    parts = [np.array_split(np.arange(tr.n), 4) for tr in traces]
+    for k in range(4):
+        for i, (st, tr) in enumerate(zip(sts, traces)):
+            if i == 0 and k == 2:
+                with pytest.raises(rv.RVError) as e:
+                    st.push(tr.key[:10], np.full(10, 7, dtype=np.uint8))
+                assert e.value.status == rv.RV_EINVAL
+            _push(rv, st, tr.key[parts[i][k]], tr.pred[parts[i][k]])
+    got = _drain(sts, [4, 4, 4])
+    for i, tr in enumerate(traces):
+        o = oracle_verify(C1, Schema(synth.SOCKET_CODES), tr.key, tr.pred)
+        assert [v.ticket for v in got[i]] == [1, 2, 3, 4]
+        assert got[i][-1].root == o.root and got[i][-1].root_counts == o.root_counts
+    svc.close()
