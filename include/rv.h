@@ -240,14 +240,23 @@ rv_status rv_combine_results(const rv_formula* f, const rv_result* parts, int n_
  *   rv_batch_run: key/pred/ws/dev_results are device pointers; results
  *     rv_result[nt * nf] land in dev_results after s completes.  The launch
  *     sequence is captured once per argument set and replayed as a graph.
- *     A result's status RV_EAGAIN means a bucket held more than 512 bindings:
- *     rerun with a smaller bucket_records.
+ *     Cluster thresholds: a trace's bindings are hashed into buckets of about
+ *     bucket_records records, whose bindings one CTA folds (lane = formula,
+ *     in passes of at most 512 bindings each); a bucket longer than
+ *     long_records (its runs too long for one CTA) is cut into segments of
+ *     long_records records: later segments are folded by CTAs of their own
+ *     into composed 64-bit transition maps (Sec. 4.2 composes monitors per
+ *     binding; here per segment), which the bucket's fold applies in order.
+ *     A result's status: RV_EINVAL (predicate code out of range),
+ *     RV_ETIMEOUT (a bounded device wait gave up), RV_EINTERNAL.
  *   rv_batch_autotune: times the candidate bucket sizes and warp-tile lengths
- *     on the given inputs, keeps the fastest and reports it in *chosen. */
+ *     on the given inputs, then the candidate long_records with the best of
+ *     those, keeps the fastest and reports it in *chosen. */
 typedef struct rv_batch rv_batch;
 typedef struct {
   int bucket_records;   /* target records per bucket (per trace), default 4096 */
   int tile_events;      /* events per warp tile of the split, default 16384 */
+  int long_records;     /* segment length of long buckets, default 65536; < 0: never split */
 } rv_batch_opts;
 rv_status rv_batch_create(const rv_formula* const* f, int nf, int nt, const uint64_t* offsets,
                           const rv_batch_opts* opts, rv_batch** out);

@@ -44,7 +44,9 @@ constexpr int MAXL = 16;              // letters per formula in batched mode
 constexpr int MAXBITS = 11;           // at most 2048 buckets per trace
 constexpr int FW = 4;                 // warps per CTA in k_bfold
 constexpr int CHUNK = 4096;           // records sorted at once in k_bfold
-constexpr int BSLOTS = 512;           // bindings per bucket held in shared memory
+constexpr int BSLOTS = 512;           // bindings per pass over a bucket held in shared memory
+constexpr int SSLOTS = 32;            // bindings of a long bucket's segment kept as composed maps
+constexpr int MAXPASSBITS = 16;       // a bucket's bindings split into at most 2^16 passes
 constexpr int BHT_BITS = 10;
 constexpr int BHT = 1 << BHT_BITS;
 constexpr uint16_t NO_SLOT = 0xFFFF, FULL_SLOT = 0xFFFE;
@@ -232,8 +234,17 @@ k_bscatter(BatchDev d, const uint32_t* key, const uint8_t* pred, const uint32_t*
 }
 
 // ------------------------------------------------------------------ fold of one bucket
+// A long bucket's segment s >= 1 folded into composed maps: one per binding
+// and formula (map of the segment's letters, starting from the identity).
+struct Slab {
+  uint32_t n, valid;             // valid = 0: more than SSLOTS bindings, fold the records instead
+  uint32_t keys[SSLOTS];
+  uint64_t maps[SSLOTS][MAXF];
+};
+
 struct BFoldShared {
   uint64_t lmap[MAXL][MAXF];
+  uint64_t smap[SSLOTS][MAXF];   // segment maps (long-bucket segments)
   uint8_t labels[MAXF][16];
   uint64_t tkey[BHT];            // key | 1 << 32 once claimed, 0 when empty
   uint16_t tslot[BHT];
@@ -245,10 +256,20 @@ struct BFoldShared {
   uint32_t seg[BSLOTS + 1];
   uint32_t fcount[MAXF][6];
   uint32_t tsum[FW * 32];
-  unsigned int nslots, ovf, next;
+  uint32_t pass_bits[MAXPASSBITS + 2], pass_val[MAXPASSBITS + 2];
+  unsigned int nslots, ovf, next, npass;
 };
 
-__device__ int bfind_or_insert(BFoldShared& S, uint32_t key, unsigned int* err) {
+// the bindings a pass over a bucket folds: low `bits` bits of the key's mix
+// (the bucket is chosen by its top bits) equal to `val`
+__device__ __forceinline__ bool in_pass(uint32_t key, uint32_t bits, uint32_t val) {
+  return bits == 0 || (mix32(key) & ((1u << bits) - 1u)) == val;
+}
+
+// slot of `key` in the bucket's table, inserting it when absent (at most cap
+// slots); a new slot starts at q0 = 0 (states) or at the identity (maps)
+template <bool MAPS>
+__device__ int bfind_or_insert(BFoldShared& S, uint32_t key, int cap, unsigned int* err) {
   const uint64_t tag = (uint64_t)key | (1ull << 32);
   uint32_t h = (key * 0x9E3779B9u) >> (32 - BHT_BITS);
   volatile uint64_t* vk = S.tkey;
@@ -259,8 +280,9 @@ __device__ int bfind_or_insert(BFoldShared& S, uint32_t key, unsigned int* err) 
       const unsigned long long prev = atomicCAS((unsigned long long*)&S.tkey[h], 0ull, (unsigned long long)tag);
       if (prev == 0) {
         const unsigned int s = atomicAdd(&S.nslots, 1u);
-        if (s >= BSLOTS) { S.ovf = 1; __threadfence_block(); vs[h] = FULL_SLOT; return -1; }
-        for (int f = 0; f < MAXF; ++f) S.state[s][f] = 0;   // q0 = 0 for every compiled monitor
+        if (s >= (unsigned)cap) { S.ovf = 1; __threadfence_block(); vs[h] = FULL_SLOT; return -1; }
+        if (MAPS) for (int f = 0; f < MAXF; ++f) S.smap[s][f] = IDENTITY_MAP;
+        else for (int f = 0; f < MAXF; ++f) S.state[s][f] = 0;   // q0 = 0 for every compiled monitor
         __threadfence_block();
         vs[h] = (uint16_t)s;
         return (int)s;
@@ -281,103 +303,104 @@ __device__ int bfind_or_insert(BFoldShared& S, uint32_t key, unsigned int* err) 
   return -1;
 }
 
-constexpr unsigned ERR_BUCKET = 32;   // a bucket has more than BSLOTS bindings
+constexpr unsigned ERR_BUCKET = 32;   // bindings of one bucket collide in every hash bit of the passes
 
-__global__ void __launch_bounds__(FW * 32)
-k_bfold(BatchDev d, const uint64_t* recs, const uint64_t* bstart, unsigned long long* counts,
-        unsigned long long* nbind, unsigned int* err, unsigned int* next) {
-  extern __shared__ __align__(16) unsigned char bsm[];
-  BFoldShared& S = *reinterpret_cast<BFoldShared*>(bsm);
+// Fold records [r0, r1) of a bucket into the table: the bindings of pass
+// (pbits, pval) only, at most cap of them.  Chunks of CHUNK records are
+// stably counting-sorted by binding slot in shared memory; then warps walk
+// the bindings' letter runs with lane f stepping formula f: its state
+// (MAPS = false) or its composed map (MAPS = true).  Returns false when the
+// pass has more than cap bindings (nothing of the table is then valid).
+template <bool MAPS>
+__device__ bool fold_records(BFoldShared& S, const uint64_t* recs, uint64_t r0, uint64_t r1, uint32_t pbits,
+                             uint32_t pval, int cap, unsigned int* err) {
   const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31, nthr = FW * 32;
   const uint32_t lt = lanemask_lt();
-  const int nf = d.nf;
-  while (true) {
-    __syncthreads();
-    if (threadIdx.x == 0) S.next = atomicAdd(next, 1u);
-    __syncthreads();
-    const unsigned int g = S.next;
-    if (g >= (unsigned)d.NB) break;
-    const uint64_t b0 = bstart[g], b1 = bstart[g + 1];
-    if (b0 == b1) continue;
-    const uint32_t t = d.bucket_trace[g];
-    for (int i = threadIdx.x; i < MAXL * MAXF; i += nthr)
-      S.lmap[i / MAXF][i % MAXF] = d.maps[(uint64_t)t * MAXL * MAXF + i];
-    for (int i = threadIdx.x; i < MAXF * 16; i += nthr) S.labels[i / 16][i % 16] = d.labels[(uint64_t)t * MAXF * 16 + i];
-    for (int i = threadIdx.x; i < BHT; i += nthr) { S.tkey[i] = 0; S.tslot[i] = NO_SLOT; }
-    for (int i = threadIdx.x; i < MAXF * 6; i += nthr) S.fcount[i / 6][i % 6] = 0;
-    if (threadIdx.x == 0) { S.nslots = 0; S.ovf = 0; }
-    __syncthreads();
-    bool failed = false;
-    for (uint64_t c0 = b0; c0 < b1; c0 += CHUNK) {
-      const int cn = (int)min((uint64_t)CHUNK, b1 - c0);
-      // 1. binding slot of every record of the chunk
-      for (int i = threadIdx.x; i < cn; i += nthr) {
-        const uint64_t r = recs[c0 + i];
-        const int sl = bfind_or_insert(S, (uint32_t)(r >> 8), err);
-        S.slot_of[i] = (uint16_t)(sl < 0 ? 0 : sl);
-        S.letter[i] = (uint8_t)(r & 0xFF);
+  for (uint64_t c0 = r0; c0 < r1; c0 += CHUNK) {
+    const int cn = (int)min((uint64_t)CHUNK, r1 - c0);
+    // 1. binding slot of every record of the chunk (NO_SLOT: not in this pass)
+    for (int i = threadIdx.x; i < cn; i += nthr) {
+      const uint64_t r = recs[c0 + i];
+      const uint32_t key = (uint32_t)(r >> 8);
+      int sl = NO_SLOT;
+      if (in_pass(key, pbits, pval)) {
+        sl = bfind_or_insert<MAPS>(S, key, cap, err);
+        if (sl < 0) sl = 0;
       }
-      for (int i = threadIdx.x; i < FW * BSLOTS; i += nthr) S.wcnt[i / BSLOTS][i % BSLOTS] = 0;
-      __syncthreads();
-      if (S.ovf) { failed = true; break; }
-      const int nsl = (int)S.nslots;
-      // 2. stable counting sort by slot; warp w owns records [w0, w1) of the chunk
-      const int per = (cn + FW - 1) / FW;
-      const int w0 = min(cn, wl * per), w1 = min(cn, w0 + per);
-      for (int i = w0 + lane; i < w1; i += 32) atomicAdd(&S.wcnt[wl][S.slot_of[i]], 1u);
-      __syncthreads();
-      // exclusive scan over (slot, warp): each thread owns 4 consecutive slots
-      {
-        const int s0 = threadIdx.x * 4;
-        uint32_t tot[4], sum = 0;
+      S.slot_of[i] = (uint16_t)sl;
+      S.letter[i] = (uint8_t)(r & 0xFF);
+    }
+    for (int i = threadIdx.x; i < FW * BSLOTS; i += nthr) S.wcnt[i / BSLOTS][i % BSLOTS] = 0;
+    __syncthreads();
+    if (S.ovf) return false;
+    const int nsl = (int)S.nslots;
+    // 2. stable counting sort by slot; warp w owns records [w0, w1) of the chunk
+    const int per = (cn + FW - 1) / FW;
+    const int w0 = min(cn, wl * per), w1 = min(cn, w0 + per);
+    for (int i = w0 + lane; i < w1; i += 32)
+      if (S.slot_of[i] != NO_SLOT) atomicAdd(&S.wcnt[wl][S.slot_of[i]], 1u);
+    __syncthreads();
+    // exclusive scan over (slot, warp): each thread owns 4 consecutive slots
+    {
+      const int s0 = threadIdx.x * 4;
+      uint32_t tot[4], sum = 0;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int sl = s0 + j;
-          uint32_t x = 0;
-          if (sl < BSLOTS)
-            for (int w = 0; w < FW; ++w) x += S.wcnt[w][sl];
-          tot[j] = x;
-          sum += x;
-        }
-        uint32_t x = sum;
-        for (int o = 1; o < 32; o <<= 1) {
-          const uint32_t y = __shfl_up_sync(FULL, x, o);
-          if (lane >= o) x += y;
-        }
-        if (lane == 31) S.tsum[wl] = x;
-        __syncthreads();
-        uint32_t wbase = 0;
-        for (int w = 0; w < wl; ++w) wbase += S.tsum[w];
-        uint32_t run = wbase + x - sum;
+      for (int j = 0; j < 4; ++j) {
+        const int sl = s0 + j;
+        uint32_t x = 0;
+        if (sl < BSLOTS)
+          for (int w = 0; w < FW; ++w) x += S.wcnt[w][sl];
+        tot[j] = x;
+        sum += x;
+      }
+      uint32_t x = sum;
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += y;
+      }
+      if (lane == 31) S.tsum[wl] = x;
+      __syncthreads();
+      uint32_t wbase = 0, all = 0;
+      for (int w = 0; w < FW; ++w) { if (w < wl) wbase += S.tsum[w]; all += S.tsum[w]; }
+      uint32_t run = wbase + x - sum;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int sl = s0 + j;
-          if (sl < BSLOTS) {
-            S.seg[sl] = run;
-            uint32_t r2 = run;
-            for (int w = 0; w < FW; ++w) { const uint32_t c = S.wcnt[w][sl]; S.wcnt[w][sl] = r2; r2 += c; }
-          }
-          run += tot[j];
+      for (int j = 0; j < 4; ++j) {
+        const int sl = s0 + j;
+        if (sl < BSLOTS) {
+          S.seg[sl] = run;
+          uint32_t r2 = run;
+          for (int w = 0; w < FW; ++w) { const uint32_t c = S.wcnt[w][sl]; S.wcnt[w][sl] = r2; r2 += c; }
         }
-        if (threadIdx.x == 0) S.seg[BSLOTS] = (uint32_t)cn;
+        run += tot[j];
       }
-      __syncthreads();
-      for (int base = w0; base < w1; base += 32) {
-        const int i = base + lane;
-        const bool v = i < w1;
-        const uint32_t sl = v ? S.slot_of[i] : 0u;
-        const uint32_t peers = match_bits<10>(sl, v);
-        uint32_t pos = 0;
-        if (v) pos = S.wcnt[wl][sl] + __popc(peers & lt);
-        __syncwarp();
-        if (v && lane == __ffs(peers) - 1) S.wcnt[wl][sl] += __popc(peers);
-        __syncwarp();
-        if (v) S.sorted[pos] = S.letter[i];
-      }
-      __syncthreads();
-      // 3. walk every binding's letters: lane f steps formula f
-      for (int sl = wl; sl < nsl; sl += FW) {
-        const uint32_t lo = S.seg[sl], hi = (sl + 1 < BSLOTS) ? S.seg[sl + 1] : (uint32_t)cn;
+      if (threadIdx.x == 0) S.seg[BSLOTS] = all;   // records of this pass in the chunk
+    }
+    __syncthreads();
+    for (int base = w0; base < w1; base += 32) {
+      const int i = base + lane;
+      const uint32_t sl = i < w1 ? S.slot_of[i] : (uint32_t)NO_SLOT;
+      const bool v = sl != NO_SLOT;
+      const uint32_t peers = match_bits<10>(v ? sl : 0u, v);
+      uint32_t pos = 0;
+      if (v) pos = S.wcnt[wl][sl] + __popc(peers & lt);
+      __syncwarp();
+      if (v && lane == __ffs(peers) - 1) S.wcnt[wl][sl] += __popc(peers);
+      __syncwarp();
+      if (v) S.sorted[pos] = S.letter[i];
+    }
+    __syncthreads();
+    // 3. walk every binding's letters: lane f steps formula f
+    for (int sl = wl; sl < nsl; sl += FW) {
+      const uint32_t lo = S.seg[sl], hi = S.seg[sl + 1];
+      if (MAPS) {
+        uint64_t M = S.smap[sl][lane];
+        for (uint32_t base = lo; base < hi; base += 32) {
+          const uint32_t n = min(32u, hi - base);
+          const uint32_t mine = lane < n ? S.sorted[base + lane] : 0u;
+          for (uint32_t j = 0; j < n; ++j) M = compose16(M, S.lmap[__shfl_sync(FULL, mine, j)][lane]);
+        }
+        S.smap[sl][lane] = M;
+      } else {
         uint32_t st = S.state[sl][lane];
         for (uint32_t base = lo; base < hi; base += 32) {
           const uint32_t n = min(32u, hi - base);
@@ -399,29 +422,170 @@ k_bfold(BatchDev d, const uint64_t* recs, const uint64_t* bstart, unsigned long 
         }
         S.state[sl][lane] = (uint8_t)st;
       }
-      __syncthreads();
     }
-    if (failed) {
-      if (threadIdx.x == 0) atomicOr(err, ERR_BUCKET);
+    __syncthreads();
+  }
+  return true;
+}
+
+__device__ void load_tables(BFoldShared& S, const BatchDev& d, uint32_t t) {
+  for (int i = threadIdx.x; i < MAXL * MAXF; i += FW * 32)
+    S.lmap[i / MAXF][i % MAXF] = d.maps[(uint64_t)t * MAXL * MAXF + i];
+  for (int i = threadIdx.x; i < MAXF * 16; i += FW * 32)
+    S.labels[i / 16][i % 16] = d.labels[(uint64_t)t * MAXF * 16 + i];
+}
+
+__device__ void reset_table(BFoldShared& S) {
+  for (int i = threadIdx.x; i < BHT; i += FW * 32) { S.tkey[i] = 0; S.tslot[i] = NO_SLOT; }
+  if (threadIdx.x == 0) { S.nslots = 0; S.ovf = 0; }
+}
+
+// Long buckets (more than long_records records) are cut into segments of
+// long_records records; segment s >= 1 of such a bucket is work item
+// item_base[g] + s - 1.  This is the cluster-size threshold above which a
+// bucket's runs are split across CTAs: each later segment is folded into
+// composed maps by a CTA of its own (k_bseg), and the bucket's fold applies
+// them in order after folding segment 0 from q0.
+__global__ void k_bextra(const uint64_t* bstart, int NB, uint64_t long_records, uint64_t* extra) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= NB) return;
+  const uint64_t len = bstart[g + 1] - bstart[g];
+  extra[g] = len > long_records ? (len + long_records - 1) / long_records - 1 : 0;
+}
+
+__global__ void __launch_bounds__(FW * 32)
+k_bseg(BatchDev d, const uint64_t* recs, const uint64_t* bstart, const uint64_t* item_base, uint64_t long_records,
+       Slab* slabs, unsigned int* err, unsigned int* next) {
+  extern __shared__ __align__(16) unsigned char bsm[];
+  BFoldShared& S = *reinterpret_cast<BFoldShared*>(bsm);
+  const uint64_t total = item_base[d.NB];
+  while (true) {
+    __syncthreads();
+    if (threadIdx.x == 0) S.next = atomicAdd(next, 1u);
+    __syncthreads();
+    const uint64_t u = S.next;
+    if (u >= total) break;
+    int lo = 0, hi = d.NB - 1;               // the bucket g with item_base[g] <= u < item_base[g + 1]
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (item_base[mid] <= u) lo = mid; else hi = mid - 1;
+    }
+    const int g = lo;
+    const uint64_t sidx = u - item_base[g] + 1;
+    const uint64_t r0 = bstart[g] + sidx * long_records, r1 = min(bstart[g + 1], r0 + long_records);
+    load_tables(S, d, d.bucket_trace[g]);
+    reset_table(S);
+    __syncthreads();
+    const bool ok = fold_records<true>(S, recs, r0, r1, 0, 0, SSLOTS, err);
+    Slab& out = slabs[u];
+    if (!ok) {
+      if (threadIdx.x == 0) { out.valid = 0; out.n = 0; }
       continue;
     }
-    // 4. verdict counts per formula
-    uint32_t c[6] = {0, 0, 0, 0, 0, 0};
     const int nsl = (int)S.nslots;
-    for (int sl = wl; sl < nsl; sl += FW) {
-      const uint32_t v = S.labels[lane][S.state[sl][lane] & 15];
-#pragma unroll
-      for (int k = 0; k < 6; ++k) c[k] += v == (uint32_t)k;
+    for (int i = threadIdx.x; i < BHT; i += FW * 32) {
+      const uint16_t sl = S.tslot[i];
+      if (sl != NO_SLOT && sl != FULL_SLOT) out.keys[sl] = (uint32_t)S.tkey[i];
     }
-#pragma unroll
-    for (int k = 0; k < 6; ++k)
-      if (c[k]) atomicAdd(&S.fcount[lane][k], c[k]);
+    for (int i = threadIdx.x; i < nsl * MAXF; i += FW * 32) out.maps[i / MAXF][i % MAXF] = S.smap[i / MAXF][i % MAXF];
+    if (threadIdx.x == 0) { out.n = (uint32_t)nsl; out.valid = 1; }
+  }
+}
+
+// Apply segment u's slab to the pass's bindings (new ones start at q0);
+// false when the pass's table overflows.
+__device__ bool apply_slab(BFoldShared& S, const Slab& sb, uint32_t pbits, uint32_t pval, unsigned int* err) {
+  const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n = (int)sb.n;
+  for (int e = wl; e < n; e += FW) {
+    const uint32_t key = sb.keys[e];
+    if (!in_pass(key, pbits, pval)) continue;
+    int sl = 0;
+    if (lane == 0) sl = bfind_or_insert<false>(S, key, BSLOTS, err);
+    sl = __shfl_sync(FULL, sl, 0);
+    if (sl < 0) continue;
+    S.state[sl][lane] = (uint8_t)step_state(S.state[sl][lane], sb.maps[e][lane]);
+  }
+  __syncthreads();
+  return !S.ovf;
+}
+
+__global__ void __launch_bounds__(FW * 32)
+k_bfold(BatchDev d, const uint64_t* recs, const uint64_t* bstart, const uint64_t* item_base, uint64_t long_records,
+        const Slab* slabs, unsigned long long* counts, unsigned long long* nbind, unsigned int* err,
+        unsigned int* next) {
+  extern __shared__ __align__(16) unsigned char bsm[];
+  BFoldShared& S = *reinterpret_cast<BFoldShared*>(bsm);
+  const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31, nthr = FW * 32;
+  const int nf = d.nf;
+  while (true) {
     __syncthreads();
+    if (threadIdx.x == 0) S.next = atomicAdd(next, 1u);
+    __syncthreads();
+    const unsigned int g = S.next;
+    if (g >= (unsigned)d.NB) break;
+    const uint64_t b0 = bstart[g], b1 = bstart[g + 1];
+    if (b0 == b1) continue;
+    const uint32_t t = d.bucket_trace[g];
+    const uint64_t first_item = item_base[g], n_extra = item_base[g + 1] - first_item;
+    const uint64_t seg0_end = n_extra ? b0 + long_records : b1;
+    load_tables(S, d, t);
+    for (int i = threadIdx.x; i < MAXF * 6; i += nthr) S.fcount[i / 6][i % 6] = 0;
+    if (threadIdx.x == 0) { S.npass = 1; S.pass_bits[0] = 0; S.pass_val[0] = 0; }
+    __syncthreads();
+    unsigned long long bound = 0;
+    // passes over subsets of the bucket's bindings, split further whenever
+    // one holds more than BSLOTS of them
+    while (S.npass > 0) {
+      const uint32_t pbits = S.pass_bits[S.npass - 1], pval = S.pass_val[S.npass - 1];
+      reset_table(S);
+      __syncthreads();
+      bool ok = fold_records<false>(S, recs, b0, seg0_end, pbits, pval, BSLOTS, err);
+      for (uint64_t k = 0; ok && k < n_extra; ++k) {
+        const Slab& sb = slabs[first_item + k];
+        if (sb.valid) {
+          ok = apply_slab(S, sb, pbits, pval, err);
+        } else {
+          const uint64_t r0 = b0 + (k + 1) * long_records;
+          ok = fold_records<false>(S, recs, r0, min(b1, r0 + long_records), pbits, pval, BSLOTS, err);
+        }
+      }
+      __syncthreads();
+      if (!ok) {
+        if (threadIdx.x == 0) {
+          S.npass -= 1;
+          if (pbits >= MAXPASSBITS) {
+            atomicOr(err, ERR_BUCKET);
+          } else {
+            S.pass_bits[S.npass] = pbits + 1; S.pass_val[S.npass] = pval;
+            S.pass_bits[S.npass + 1] = pbits + 1; S.pass_val[S.npass + 1] = pval | (1u << pbits);
+            S.npass += 2;
+          }
+        }
+        __syncthreads();
+        continue;
+      }
+      // 4. verdict counts per formula of this pass's bindings
+      uint32_t c[6] = {0, 0, 0, 0, 0, 0};
+      const int nsl = (int)S.nslots;
+      for (int sl = wl; sl < nsl; sl += FW) {
+        const uint32_t v = S.labels[lane][S.state[sl][lane] & 15];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) c[k] += v == (uint32_t)k;
+      }
+#pragma unroll
+      for (int k = 0; k < 6; ++k)
+        if (c[k]) atomicAdd(&S.fcount[lane][k], c[k]);
+      bound += (unsigned long long)nsl;
+      __syncthreads();
+      if (threadIdx.x == 0) S.npass -= 1;
+      __syncthreads();
+    }
     for (int i = threadIdx.x; i < nf * 6; i += nthr) {
       const uint32_t x = S.fcount[i / 6][i % 6];
       if (x) atomicAdd(&counts[((uint64_t)t * nf + i / 6) * 6 + i % 6], (unsigned long long)x);
     }
-    if (threadIdx.x == 0) atomicAdd(&nbind[t], (unsigned long long)nsl);
+    if (threadIdx.x == 0) atomicAdd(&nbind[t], bound);
   }
 }
 
@@ -440,7 +604,7 @@ __global__ void k_broot(BatchDev d, const unsigned long long* counts, const unsi
   r.n_nodes[0] = nbind[t];
   r.events = d.offsets[t + 1] - d.offsets[t];
   const unsigned e = *err;
-  r.status = (e & ERR_LETTER) ? RV_EINVAL : (e & ERR_BUCKET) ? RV_EAGAIN : e ? RV_EINTERNAL : RV_OK;
+  r.status = (e & ERR_LETTER) ? RV_EINVAL : (e & ERR_SPIN) ? RV_ETIMEOUT : e ? RV_EINTERNAL : RV_OK;
   out[i] = r;
 }
 
@@ -462,6 +626,7 @@ struct rv_batch {
   std::vector<uint32_t> nletters; // [nt]
   int bucket_records = 4096;
   int tile_events = 16384;
+  int long_records = 1 << 16;     // 0: no long-bucket segments
   // device plan (rebuilt when the tuning changes)
   void* plan = nullptr;
   size_t plan_bytes = 0;
@@ -479,8 +644,12 @@ struct rv_batch {
 namespace {
 
 struct BatchLayout {
-  size_t o_hist, o_tot, o_bstart, o_recs, o_counts, o_nbind, o_err, o_next, total;
+  size_t o_hist, o_tot, o_bstart, o_recs, o_extra, o_item, o_slabs, o_counts, o_nbind, o_err, o_next, o_next2, total;
+  uint64_t max_items;
 };
+
+// long_records as the kernels see it: 0 turns the segments off
+uint64_t long_len(int long_records) { return long_records > 0 ? (uint64_t)long_records : ~0ull >> 1; }
 
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -504,7 +673,7 @@ void plan_shape(const rv_batch* b, int bucket_records, int tile_events, std::vec
   *hist_entries = hist;
 }
 
-BatchLayout layout(const rv_batch* b, int NB, size_t hist_entries) {
+BatchLayout layout(const rv_batch* b, int NB, size_t hist_entries, int long_records) {
   BatchLayout L{};
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t r = off; off = a256(off + bytes); return r; };
@@ -513,10 +682,16 @@ BatchLayout layout(const rv_batch* b, int NB, size_t hist_entries) {
   L.o_tot = take((size_t)NB * 8);
   L.o_bstart = take((size_t)(NB + 1) * 8);
   L.o_recs = take(std::max<uint64_t>(n, 1) * 8);
-  L.o_counts = take((size_t)b->nt * b->nf * 6 * 8);
+  L.o_extra = take((size_t)NB * 8);
+  L.o_item = take((size_t)(NB + 1) * 8);
+  // every extra segment holds long_records records of its bucket before it
+  L.max_items = long_records > 0 ? n / (uint64_t)long_records + 1 : 0;
+  L.o_slabs = take(std::max<uint64_t>(L.max_items, 1) * sizeof(Slab));
+  L.o_counts = take((size_t)b->nt * b->nf * 6 * 8);   // from here on zeroed before every run
   L.o_nbind = take((size_t)b->nt * 8);
   L.o_err = take(4);
   L.o_next = take(4);
+  L.o_next2 = take(4);
   L.total = off;
   return L;
 }
@@ -588,7 +763,7 @@ int num_sms_b() { return rv_num_sms(); }
 rv_status enqueue(rv_batch* b, const uint32_t* key, const uint8_t* pred, unsigned char* ws, rv_result* res,
                   cudaStream_t s) {
   const BatchDev& d = b->dev;
-  const BatchLayout L = layout(b, d.NB, b->hist_entries);
+  const BatchLayout L = layout(b, d.NB, b->hist_entries, b->long_records);
   uint32_t* hist = (uint32_t*)(ws + L.o_hist);
   uint64_t* tot = (uint64_t*)(ws + L.o_tot);
   uint64_t* bstart = (uint64_t*)(ws + L.o_bstart);
@@ -597,6 +772,11 @@ rv_status enqueue(rv_batch* b, const uint32_t* key, const uint8_t* pred, unsigne
   unsigned long long* nbind = (unsigned long long*)(ws + L.o_nbind);
   unsigned int* err = (unsigned int*)(ws + L.o_err);
   unsigned int* next = (unsigned int*)(ws + L.o_next);
+  unsigned int* next2 = (unsigned int*)(ws + L.o_next2);
+  uint64_t* extra = (uint64_t*)(ws + L.o_extra);
+  uint64_t* item_base = (uint64_t*)(ws + L.o_item);
+  Slab* slabs = (Slab*)(ws + L.o_slabs);
+  const uint64_t lr = long_len(b->long_records);
   BCU(cudaMemsetAsync(ws + L.o_counts, 0, L.total - L.o_counts, s));   // counts, nbind, err, next
   const int tb = (d.ntiles + BW - 1) / BW;
   if (d.ntiles) {
@@ -604,8 +784,14 @@ rv_status enqueue(rv_batch* b, const uint32_t* key, const uint8_t* pred, unsigne
     RV_LAUNCH("k_bscan", k_bscan, (d.NB + 255) / 256, 256, 0, s, d, hist, tot);
     RV_LAUNCH("k_scan64", k_scan64, 1, 1024, 0, s, tot, d.NB, bstart);
     RV_LAUNCH("k_bscatter", k_bscatter, tb, BW * 32, 0, s, d, key, pred, hist, bstart, recs);
+    RV_LAUNCH("k_bextra", k_bextra, (d.NB + 255) / 256, 256, 0, s, bstart, d.NB, lr, extra);
+    RV_LAUNCH("k_scan64", k_scan64, 1, 1024, 0, s, extra, d.NB, item_base);
     const int grid = std::min(d.NB, num_sms_b() * 4);
-    RV_LAUNCH("k_bfold", k_bfold, grid, FW * 32, sizeof(BFoldShared), s, d, recs, bstart, counts, nbind, err, next);
+    if (L.max_items)
+      RV_LAUNCH("k_bseg", k_bseg, (int)std::min<uint64_t>(L.max_items, (uint64_t)num_sms_b() * 4), FW * 32,
+                sizeof(BFoldShared), s, d, recs, bstart, item_base, lr, slabs, err, next2);
+    RV_LAUNCH("k_bfold", k_bfold, grid, FW * 32, sizeof(BFoldShared), s, d, recs, bstart, item_base, lr, slabs,
+              counts, nbind, err, next);
   }
   RV_LAUNCH("k_broot", k_broot, (d.nt * d.nf + 127) / 128, 128, 0, s, d, counts, nbind, err, res);
   BCU(cudaGetLastError());
@@ -651,6 +837,7 @@ extern "C" rv_status rv_batch_create(const rv_formula* const* f, int nf, int nt,
   }
   if (opts && opts->bucket_records) b->bucket_records = opts->bucket_records;
   if (opts && opts->tile_events) b->tile_events = std::max(1024, opts->tile_events);
+  if (opts && opts->long_records) b->long_records = opts->long_records < 0 ? 0 : std::max(CHUNK, opts->long_records);
   rv_status st = build_plan(b);
   if (st) { rv_batch_free(b); return st; }
   *out = b;
@@ -665,7 +852,8 @@ extern "C" size_t rv_batch_workspace_size(const rv_batch* b) {
       int NB = 0;
       size_t he = 0;
       plan_shape(b, br, te, nullptr, nullptr, &NB, &he);
-      worst = std::max(worst, layout(b, NB, he).total);
+      for (int lr : {b->long_records, 16384})
+        worst = std::max(worst, layout(b, NB, he, lr).total);
     }
   return worst;
 }
@@ -673,6 +861,7 @@ extern "C" size_t rv_batch_workspace_size(const rv_batch* b) {
 // the attribute applies to the current device: set it once per device
 static rv_status set_bfold_attr() {
   BCU(cudaFuncSetAttribute(k_bfold, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BFoldShared)));
+  BCU(cudaFuncSetAttribute(k_bseg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BFoldShared)));
   return RV_OK;
 }
 
@@ -680,7 +869,7 @@ extern "C" rv_status rv_batch_run(rv_batch* b, const uint32_t* key, const uint8_
                                   rv_result* dev_results, cudaStream_t s) {
   if (!b || !ws || !dev_results || (b->offsets.back() && (!key || !pred)))
     return rv_fail(RV_EINVAL, "null argument");
-  const BatchLayout L = layout(b, b->dev.NB, b->hist_entries);
+  const BatchLayout L = layout(b, b->dev.NB, b->hist_entries, b->long_records);
   if (ws_bytes < L.total) return rv_fail(RV_ENOMEM, "workspace of %zu bytes, need %zu", ws_bytes, L.total);
   if (rv_status st = rv_once_per_device(RV_ONCE_BATCH, &set_bfold_attr)) return st;
   if (rv_prof_enabled())   // per-kernel events need eager launches, not a graph replay
@@ -704,42 +893,59 @@ extern "C" rv_status rv_batch_run(rv_batch* b, const uint32_t* key, const uint8_
   return RV_OK;
 }
 
+// Times the launch sequence on the caller's inputs for each candidate and
+// keeps the fastest: first the bucket size (t1: a bucket's bindings are
+// folded by one CTA, lane = formula) and the warp tile of the split, then,
+// with those, the long-bucket threshold (t2: longer buckets are cut into
+// segments folded by separate CTAs through composed maps; 0 = never).
 extern "C" rv_status rv_batch_autotune(rv_batch* b, const uint32_t* key, const uint8_t* pred, void* ws,
                                        size_t ws_bytes, rv_result* dev_results, cudaStream_t s,
                                        rv_batch_opts* chosen) {
   if (!b || !dev_results) return rv_fail(RV_EINVAL, "null argument");
   const int cand_br[] = {1024, 2048, 4096, 8192};
   const int cand_te[] = {8192, 32768};
+  const int cand_lr[] = {16384, 65536, 262144, 0};
   float best = 1e30f;
-  int best_br = b->bucket_records, best_te = b->tile_events;
+  int best_br = b->bucket_records, best_te = b->tile_events, best_lr = b->long_records;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   rv_status st = RV_OK;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
     st = rv_fail(RV_ECUDA, "event creation failed");
-  for (int br : cand_br) {
-    for (int te : cand_te) {
-      if (st) break;
-      b->bucket_records = br;
-      b->tile_events = te;
-      if ((st = build_plan(b))) break;
-      if ((st = rv_batch_run(b, key, pred, ws, ws_bytes, dev_results, s))) break;   // capture + warm-up
-      float ms = 0.f;
-      if (cudaEventRecord(e0, s) != cudaSuccess) { st = rv_fail(RV_ECUDA, "event record"); break; }
-      for (int r = 0; r < 3 && !st; ++r) st = rv_batch_run(b, key, pred, ws, ws_bytes, dev_results, s);
-      if (st || cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-          cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
-        if (!st) st = rv_fail(RV_ECUDA, "timing failed");
-        break;
-      }
-      if (ms < best) { best = ms; best_br = br; best_te = te; }
+  auto trial = [&](int br, int te, int lr) -> bool {
+    b->bucket_records = br;
+    b->tile_events = te;
+    b->long_records = lr;
+    if ((st = build_plan(b))) return false;
+    if ((st = rv_batch_run(b, key, pred, ws, ws_bytes, dev_results, s))) return false;   // capture + warm-up
+    float ms = 0.f;
+    if (cudaEventRecord(e0, s) != cudaSuccess) { st = rv_fail(RV_ECUDA, "event record"); return false; }
+    for (int r = 0; r < 3 && !st; ++r) st = rv_batch_run(b, key, pred, ws, ws_bytes, dev_results, s);
+    if (st || cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      if (!st) st = rv_fail(RV_ECUDA, "timing failed");
+      return false;
     }
-  }
+    if (ms < best) { best = ms; best_br = br; best_te = te; best_lr = lr; }
+    return true;
+  };
+  const int lr0 = b->long_records;
+  for (int br : cand_br)
+    for (int te : cand_te)
+      if (!st && !trial(br, te, lr0)) break;
+  const int br1 = best_br, te1 = best_te;
+  for (int lr : cand_lr)
+    if (!st && lr != lr0 && !trial(br1, te1, lr)) break;
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   b->bucket_records = best_br;
   b->tile_events = best_te;
+  b->long_records = best_lr;
   const rv_status st2 = build_plan(b);
-  if (chosen) { chosen->bucket_records = best_br; chosen->tile_events = best_te; }
+  if (chosen) {
+    chosen->bucket_records = best_br;
+    chosen->tile_events = best_te;
+    chosen->long_records = best_lr > 0 ? best_lr : -1;
+  }
   return st ? st : st2;
 }
 

@@ -347,7 +347,7 @@ def combine_results(formula: Formula, parts) -> Result:
 
 # ---------------------------------------------------------------------- batched
 class _BatchOpts(ctypes.Structure):
-    _fields_ = [("bucket_records", ctypes.c_int), ("tile_events", ctypes.c_int)]
+    _fields_ = [("bucket_records", ctypes.c_int), ("tile_events", ctypes.c_int), ("long_records", ctypes.c_int)]
 
 
 def _batch_sigs(L):
@@ -369,7 +369,7 @@ class Batch:
     """Many traces (concatenated, CSR offsets) x nf formulas per trace, run as
     one captured graph (rv_batch_*)."""
 
-    def __init__(self, formulas, offsets, bucket_records=0, tile_events=0):
+    def __init__(self, formulas, offsets, bucket_records=0, tile_events=0, long_records=0):
         L = lib()
         _batch_sigs(L)
         self.nt = len(formulas)
@@ -378,7 +378,7 @@ class Batch:
         flat = (ctypes.c_void_p * (self.nt * self.nf))(*[f.handle.value for fs in formulas for f in fs])
         self.offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
         h = ctypes.c_void_p()
-        opts = _BatchOpts(bucket_records, tile_events)
+        opts = _BatchOpts(bucket_records, tile_events, long_records)
         _check(L.rv_batch_create(flat, self.nf, self.nt, self.offsets.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
                                  ctypes.byref(opts), ctypes.byref(h)))
         self._h = h
@@ -397,7 +397,7 @@ class Batch:
                                        ctypes.c_void_p(ws.data_ptr()), ws.numel(),
                                        ctypes.c_void_p(dev_results.data_ptr()), _stream_handle(stream),
                                        ctypes.byref(ch)))
-        return {"bucket_records": ch.bucket_records, "tile_events": ch.tile_events}
+        return {"bucket_records": ch.bucket_records, "tile_events": ch.tile_events, "long_records": ch.long_records}
 
     def results(self, dev_results):
         raw = bytes(dev_results.cpu().numpy())

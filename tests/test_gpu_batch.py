@@ -93,16 +93,79 @@ def test_batch_bad_predicate(rv):
     assert all(r.status == rv.RV_EINVAL for r in out)
 
 
-def test_batch_overfull_bucket_reports_eagain(rv):
+def test_buckets_of_many_bindings_fold_in_passes(rv):
+    # every event its own binding: buckets of thousands of bindings, folded in
+    # passes of at most 512 bindings each (hash-selected subsets)
     import torch
     rng = np.random.default_rng(4)
-    n = 20000
-    keys = [np.arange(n, dtype=np.uint32)]          # every event its own binding
-    preds = [rng.integers(0, 2, size=n).astype(np.uint8)]
-    forms = [[rv.Formula("E x: p(x) => F a", ["a", "b"])]]
-    off = np.array([0, n], dtype=np.uint64)
-    _, _, _, _, _, out = _run(rv, torch, forms, keys, preds, off, bucket_records=8192)
-    assert out[0].status in (rv.RV_OK, rv.RV_EAGAIN)
-    _, _, _, _, _, out = _run(rv, torch, forms, keys, preds, off, bucket_records=256)
-    o = oracle_verify("E x: p(x) => F a", Schema(["a", "b"]), keys[0], preds[0])
-    assert out[0].status == 0 and out[0].root == o.root and out[0].root_counts == o.root_counts
+    n = 60_000
+    keys = [np.arange(n, dtype=np.uint32) * np.uint32(2654435761), rng.integers(0, 7_000, size=n).astype(np.uint32)]
+    preds = [rng.integers(0, 2, size=n).astype(np.uint8) for _ in range(2)]
+    texts = ["E x: p(x) => F a", "A_{>=0.4} x: p(x) => G(a -> X b)"]
+    forms = [[rv.Formula(t, ["a", "b"]) for t in texts] for _ in range(2)]
+    off = np.array([0, n, 2 * n], dtype=np.uint64)
+    for br in (8192, 256):
+        _, _, _, _, _, out = _run(rv, torch, forms, keys, preds, off, bucket_records=br)
+        for t in range(2):
+            for j, text in enumerate(texts):
+                o = oracle_verify(text, Schema(["a", "b"]), keys[t], preds[t])
+                r = out[t * 2 + j]
+                assert r.status == 0 and r.root == o.root and r.root_counts == o.root_counts, (br, t, j)
+                assert r.n_nodes[0] == o.n_nodes[0]
+
+
+def _zipf_head_batch(rv, seed, head_events, nf):
+    # trace 0: one binding with head_events events among 4000 light ones;
+    # traces 1..3: ordinary uniform traces
+    rng = np.random.default_rng(seed)
+    codes = ["p0", "p1", "p2"]
+    n0 = head_events + 200_000
+    k0 = rng.integers(1, 4_000, size=n0).astype(np.uint32) * np.uint32(2654435761)
+    k0[rng.random(n0) < head_events / n0] = np.uint32(77)
+    keys = [k0] + [rng.integers(0, 3_000, size=50_000).astype(np.uint32) for _ in range(3)]
+    preds = [rng.integers(0, 3, size=len(k)).astype(np.uint8) for k in keys]
+    forms, texts = [], []
+    for _ in keys:
+        f, t = _formulas(rv, rng, codes, nf)
+        forms.append(f)
+        texts.append(t)
+    off = np.zeros(len(keys) + 1, dtype=np.uint64)
+    off[1:] = np.cumsum([len(k) for k in keys])
+    return keys, preds, forms, texts, codes, off
+
+
+def test_long_cluster_segments_match_single_launch_and_oracle(rv):
+    # a binding of more than a million events: its bucket is cut into
+    # segments folded by separate CTAs into composed maps (long_records), or
+    # folded whole (long_records < 0); both equal the single-trace launch and,
+    # for some formulas, the oracle
+    import torch
+    keys, preds, forms, texts, codes, off = _zipf_head_batch(rv, 6, 1_100_000, 16)
+    assert (keys[0] == 77).sum() > 1_000_000
+    outs = []
+    for lr in (16384, 65536, -1):
+        _, _, _, _, _, out = _run(rv, torch, forms, keys, preds, off, bucket_records=4096, long_records=lr)
+        outs.append([(r.status, r.root, r.root_counts, r.n_nodes[0]) for r in out])
+    assert outs[0] == outs[1] == outs[2]
+    out = outs[0]
+    for t in range(len(keys)):
+        kt = torch.from_numpy(keys[t].view(np.int32)).cuda()
+        pt = torch.from_numpy(preds[t]).cuda()
+        for j in range(16):
+            s = rv.verify(forms[t][j], kt, pt)
+            assert out[t * 16 + j] == (0, s.root, s.root_counts, s.n_nodes[0]), (t, j)
+    for j in range(0, 16, 5):
+        o = oracle_verify(texts[0][j], Schema(codes), keys[0], preds[0])
+        assert out[j][1:3] == (o.root, o.root_counts), texts[0][j]
+
+
+def test_autotune_reports_thresholds(rv):
+    import torch
+    keys, preds, forms, texts, codes, off = _zipf_head_batch(rv, 7, 300_000, 8)
+    b, k, p, ws, res, out = _run(rv, torch, forms, keys, preds, off)
+    chosen = b.autotune(k, p, ws, res)
+    assert chosen["bucket_records"] in (1024, 2048, 4096, 8192)
+    assert chosen["long_records"] in (16384, 65536, 262144, -1)
+    b.run(k, p, ws, res)
+    torch.cuda.synchronize()
+    assert [(r.root, r.root_counts) for r in b.results(res)] == [(r.root, r.root_counts) for r in out]
