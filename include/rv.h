@@ -162,6 +162,11 @@ typedef struct {
   int unit_records;      /* records folded by one CTA, multiple of 256 */
   int no_heavy;          /* nonzero: no own sub-buckets for bindings that a sample of
                             the trace shows to be heavy (one-variable formulas) */
+  int test_wait_polls;   /* test aid, 0 in normal use: > 0 makes the last kernel wait
+                            for a device flag that nothing sets, giving up after this
+                            many polls; the result's status is then RV_ETIMEOUT, the
+                            verdicts are still computed and the context stays usable
+                            (exercises the bounded-wait path without a GPU fault) */
 } rv_verify_opts;
 
 /* Device memory the offline path needs for a trace of n events

@@ -1997,8 +1997,18 @@ k_combine(const Item* items_in, const Pair* pool_in, const Group* groups, const 
   flush_final(p, fc);
 }
 
-__global__ void k_root(const Acc* acc, Params p, uint64_t n, rv_result* out) {
+__global__ void k_root(Acc* acc, Params p, uint64_t n, rv_result* out, int test_wait_polls) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (test_wait_polls > 0) {
+    // a bounded wait on a flag that nothing sets: it gives up after the
+    // given number of polls, reports ERR_SPIN and the kernel ends normally
+    volatile unsigned int* flag = &acc->test_flag;
+    int polls = 0;
+    while (*flag == 0) {
+      if (++polls > test_wait_polls) { atomicOr(&acc->err, (unsigned)ERR_SPIN); break; }
+      __nanosleep(256);
+    }
+  }
   rv_result r;
   memset(&r, 0, sizeof r);
   for (int m = 0; m < 2; ++m) {
@@ -2019,6 +2029,7 @@ __global__ void k_root(const Acc* acc, Params p, uint64_t n, rv_result* out) {
   r.status = RV_OK;
   if (e & (ERR_LETTER | ERR_TS)) r.status = RV_EINVAL;
   else if (e & ERR_OUTER_FULL) r.status = RV_EAGAIN;   // host retries with a finer split
+  else if (e & ERR_SPIN) r.status = RV_ETIMEOUT;       // a bounded device wait gave up
   else if (e) r.status = RV_EINTERNAL;
   *out = r;
 }
@@ -2030,6 +2041,7 @@ struct Plan {
   int htbits;          // heavy routing: log2 of the sample table
   uint64_t hstride;    // heavy routing: one sample every hstride events
   bool tiled, heavy;
+  int test_wait;       // polls of the test wait in k_root (0: none)
   uint64_t n, per_warp, unit, tile2;
   uint64_t max_tiles2, max_units;
   int levels;
@@ -2048,6 +2060,7 @@ static Plan make_plan(const rv_formula* f, uint64_t n, int host_input, const rv_
                       bool stream = false) {
   Plan pl{};
   pl.n = n;
+  pl.test_wait = o && o->test_wait_polls > 0 ? o->test_wait_polls : 0;
   pl.F = f->n_quant == 2 ? FMT_K2 : (f->key_bits == 64 && f->n_quant == 1 ? FMT_K64 : FMT_K32);
   // default: 256 first-level buckets (few open write frontiers in the
   // scatter) and a second-level split down to about 8192 records per bucket
@@ -2283,7 +2296,7 @@ static rv_status launch_all(const Plan& pl, const rv_formula* f, const void* key
       std::swap(pin, pout);
     }
   }
-  if (!ss) RV_LAUNCH("k_root", k_root, 1, 32, 0, s, acc, p, n, dev_out);
+  if (!ss) RV_LAUNCH("k_root", k_root, 1, 32, 0, s, acc, p, n, dev_out, pl.test_wait);
   RV_CU(cudaGetLastError());
   return RV_OK;
 }
@@ -2437,6 +2450,7 @@ extern "C" rv_status rv_verify_trace(const rv_formula* f, const rv_trace* t, int
     *out = *pinned;
     if (out->status == RV_EAGAIN && f->n_quant == 2 && pl.B2 < 7 && !(opts && opts->sub_bucket_bits)) continue;
     if (out->status == RV_EINVAL) return rv_fail(RV_EINVAL, "trace rejected: predicate code out of range or timestamps decreasing");
+    if (out->status == RV_ETIMEOUT) return rv_fail(RV_ETIMEOUT, "a bounded device wait gave up (device status word)");
     if (out->status != RV_OK) return rv_fail((rv_status)out->status, "device status %d", out->status);
     return RV_OK;
   }

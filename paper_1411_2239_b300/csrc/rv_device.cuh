@@ -190,6 +190,7 @@ struct Acc {
   unsigned int next_unit;       // dynamic work distribution of k_fold
   unsigned int next_group[8];   // and of each k_combine level
   unsigned int n_multi;         // buckets folded by more than one unit
+  unsigned int test_flag;       // set by nothing: the bounded wait of rv_verify_opts.test_wait_polls
 };
 
 // ------------------------------------------------------------------ streaming state

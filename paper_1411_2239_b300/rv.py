@@ -59,7 +59,7 @@ class _Bindings(ctypes.Structure):
 
 class _Opts(ctypes.Structure):
     _fields_ = [("bucket_bits", ctypes.c_int), ("sub_bucket_bits", ctypes.c_int), ("unit_records", ctypes.c_int),
-                ("no_heavy", ctypes.c_int)]
+                ("no_heavy", ctypes.c_int), ("test_wait_polls", ctypes.c_int)]
 
 
 RESULT_BYTES = ctypes.sizeof(_Result)
@@ -184,7 +184,7 @@ def _opts(opts):
     if not opts:
         return None
     return ctypes.byref(_Opts(opts.get("bucket_bits", 0), opts.get("sub_bucket_bits", 0), opts.get("unit_records", 0),
-                              int(opts.get("no_heavy", 0))))
+                              int(opts.get("no_heavy", 0)), int(opts.get("test_wait_polls", 0))))
 
 
 def workspace_size(formula: Formula, n: int, host_input: bool = False, opts=None) -> int:

@@ -294,3 +294,25 @@ def test_two_devices_in_one_process(rv, torch_cuda):
     for d in (0, 1, 0):
         with torch_cuda.cuda.device(d):
             _check(rv, torch_cuda, C1, tr.codes, tr.key, tr.pred)
+
+
+def test_bounded_device_wait_gives_up_with_timeout_status(rv, torch_cuda):
+    # a wait on a device flag that nothing sets (rv_verify_opts.test_wait_polls)
+    # gives up after its polls: the result's status word says RV_ETIMEOUT, the
+    # verdict is still computed, and the context stays usable
+    tr = synth.socket_trace(50_000, 500, n_pending=20, seed=33)
+    f = rv.Formula(C1, tr.codes)
+    k, p = _dev(torch_cuda, tr.key), _dev(torch_cuda, tr.pred)
+    with pytest.raises(rv.RVError) as e:
+        rv.verify(f, k, p, opts={"test_wait_polls": 2000})
+    assert e.value.status == rv.RV_ETIMEOUT
+    ws = torch_cuda.empty(rv.workspace_size(f, tr.n), dtype=torch_cuda.uint8, device="cuda")
+    out = torch_cuda.zeros(rv.RESULT_BYTES, dtype=torch_cuda.uint8, device="cuda")
+    rv.verify_async(f, k, p, ws, out, opts={"test_wait_polls": 2000})
+    torch_cuda.cuda.synchronize()
+    r = rv.parse_result(bytes(out.cpu().numpy()))
+    good = rv.verify(f, k, p)
+    o = oracle_verify(C1, Schema(tr.codes), tr.key, tr.pred)
+    assert r.status == rv.RV_ETIMEOUT
+    assert good.status == 0 and (good.root, good.root_counts) == (o.root, o.root_counts)
+    assert (r.root, r.root_counts) == (o.root, o.root_counts)
