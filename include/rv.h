@@ -197,6 +197,30 @@ rv_status rv_verify_trace_async(const rv_formula* f, const rv_trace* t, void* ws
                                 rv_result* dev_out, const rv_bindings* bindings,
                                 const rv_verify_opts* opts, cudaStream_t s);
 
+/* ------------------------------------------------------------------ per-event timeline
+ * The online mode of Algorithm 1 (Sec. 4.2) yields an evolving verdict; this
+ * gives it at event granularity.  For event j whose innermost binding is D
+ * (its key: the 32- or 64-bit key, (d0 << 32) | d1 with two variables, one
+ * binding for an unquantified property), event_verdicts[j] is the LTL4
+ * verdict (Def. "LTL4 semantics", Sec. 2.2.2; rv_verdict code F, Fp, Tp or T)
+ * of D's projection (Sec. 2.4.3) cut after event j.  Every binding whose
+ * verdict becomes F adds one pair (viol_keys[i], viol_index[i]): its key and
+ * the trace index of its first F event (F is permanent); *n_viol receives the
+ * number of pairs, in unspecified order.
+ * t holds device arrays; event_verdicts (n bytes), viol_keys (uint64[n]),
+ * viol_index (uint32[n]) and n_viol (one uint64) are device memory owned by
+ * the caller; ws is a device workspace of rv_timeline_workspace_size bytes.
+ * Runs on stream s and returns when the results are complete (it reads a
+ * small status back).  The events are grouped by a stable radix sort of (key,
+ * index) and each binding's states come from a segmented scan of composed
+ * 64-bit transition maps, so long bindings spread over the whole GPU.
+ * Errors: RV_EINVAL (null arrays, predicate code out of range), RV_ENOMEM
+ * (workspace), RV_ECUDA. */
+size_t rv_timeline_workspace_size(const rv_formula* f, uint64_t n);
+rv_status rv_verify_timeline(const rv_formula* f, const rv_trace* t, void* ws, size_t ws_bytes,
+                             uint8_t* event_verdicts, uint64_t* viol_keys, uint32_t* viol_index,
+                             uint64_t* n_viol, cudaStream_t s);
+
 /* ------------------------------------------------------------------ one trace over several ranks
  * Algorithm 1 (Sec. 4.2) evaluates every binding on its own projection
  * (Sec. 2.4.3); all bindings of one outer value d_0 form one subtree of the

@@ -17,9 +17,12 @@ Modules
                function B, constraint S (Eq. S) and the six-valued inductive
                semantics (Def. "LTL4-C Semantics", Table 1).
   verify    -- the whole trace -> verdict function (the method's result).
+  timeline  -- the verdict of every event's binding after that event, and
+               each binding's first violation (the online mode, Sec. 4.2).
 
-Parity status: every function is pinned by tests/test_oracle_*.py except the
+Parity status: every function is pinned by tests/test_oracle_*.py; the
 readings of the six-valued valuation beyond the cases the paper works out
-(the ladder for <=/< and =, and the percentage-quantifier permanence rules),
-which are marked "parity unpinned" in counting.py.
+(the ladder for <=/< and =, the percentage-quantifier permanence rules) are
+pinned by an enumeration of how a node's children can still turn out
+(tests/test_oracle_permanence.py).
 """

@@ -1,0 +1,415 @@
+// Per-event verdict timeline and first violation of every binding.
+//
+// The online mode of Algorithm 1 (Sec. 4.2) yields an evolving verdict; here
+// it is given at event granularity: for event j of binding D (the innermost
+// value vector of the event, Sec. 2.4.1), the LTL4 verdict of D's projection
+// u^D (Sec. 2.4.3) up to and including j, i.e. lambda(delta*(q0, prefix)) of
+// the body's Moore monitor (Sec. 2.2.3), and for every binding whose verdict
+// becomes F the index of the first event at which it does (F is permanent,
+// Def. "LTL4 semantics", so that event is unique).
+//
+// Steps:
+//   sort   the events grouped by key, trace order kept inside a key: a stable
+//          LSD radix sort of (key, event index) by 8-bit key digits (digits on
+//          which every key agrees are skipped);
+//   scan   an inclusive segmented scan over the sorted events whose operator
+//          composes the letters' 64-bit transition maps ("M then m"), segment
+//          heads where the key changes.  Three phases: per tile of TT * TV
+//          events the aggregate (head seen, map since the last head); an
+//          exclusive scan of the tile aggregates; per tile again, each thread
+//          starting from its carried state and stepping states, so a binding
+//          of any length is spread over every tile it covers;
+//   emit   each event's verdict written at its trace position; a binding's
+//          first F event recorded as (key, index).
+#include <algorithm>
+#include <cstring>
+
+#include "profile.h"
+#include "rv_device.cuh"
+
+using namespace rvd;
+
+namespace {
+
+constexpr int TW = 8;                 // warps per CTA of the radix passes
+constexpr int TT = 256;               // threads per CTA of the scan
+constexpr int TV = 16;                // events per thread of the scan
+constexpr int TTILE = TT * TV;
+constexpr unsigned TFULL = 0xFFFFFFFFu;
+
+struct Agg { uint64_t map; uint32_t head, pad; };   // head: a segment starts inside
+
+// ------------------------------------------------------------------ radix passes
+template <typename K>
+__global__ void __launch_bounds__(TW * 32)
+k_t_hist(const K* key, uint64_t n, uint64_t per_warp, int G_w, int shift, uint32_t* hist) {
+  __shared__ uint32_t cnt[TW][256];
+  const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * TW + wl;
+  for (int r = lane; r < 256; r += 32) cnt[wl][r] = 0;
+  __syncwarp();
+  if (gw >= G_w) return;
+  const uint64_t begin = (uint64_t)gw * per_warp, end = min(n, begin + per_warp);
+  for (uint64_t i = begin + lane; i < end; i += 32) atomicAdd(&cnt[wl][(uint32_t)(key[i] >> shift) & 255u], 1u);
+  __syncwarp();
+  for (int r = lane; r < 256; r += 32) hist[(uint64_t)gw * 256 + r] = cnt[wl][r];
+}
+
+// one CTA per digit value: exclusive prefix of its column over the warp slices
+__global__ void __launch_bounds__(1024) k_t_colscan(uint32_t* hist, int G_w, uint64_t* tot) {
+  __shared__ uint64_t wsum[32];
+  const int r = blockIdx.x;
+  const int per = (G_w + blockDim.x - 1) / blockDim.x;
+  const int j0 = threadIdx.x * per, j1 = min(G_w, j0 + per);
+  uint64_t mine = 0;
+  for (int j = j0; j < j1; ++j) mine += hist[(uint64_t)j * 256 + r];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint64_t incl = mine;
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint64_t y = __shfl_up_sync(TFULL, incl, d);
+    if (lane >= d) incl += y;
+  }
+  if (lane == 31) wsum[w] = incl;
+  __syncthreads();
+  if (w == 0) {
+    uint64_t x = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint64_t y = __shfl_up_sync(TFULL, x, d);
+      if (lane >= d) x += y;
+    }
+    wsum[lane] = x;
+  }
+  __syncthreads();
+  uint64_t run = (w ? wsum[w - 1] : 0) + incl - mine;
+  for (int j = j0; j < j1; ++j) {
+    const uint32_t c = hist[(uint64_t)j * 256 + r];
+    hist[(uint64_t)j * 256 + r] = (uint32_t)run;
+    run += c;
+  }
+  if (threadIdx.x == blockDim.x - 1) tot[r] = run;
+}
+
+// stable placement of (key, index) by digit, behind the slice's prefix
+template <typename K>
+__global__ void __launch_bounds__(TW * 32)
+k_t_scatter(const K* key, const uint32_t* idx, uint64_t n, uint64_t per_warp, int G_w, int shift,
+            const uint32_t* pre, const uint64_t* tot, K* key_out, uint32_t* idx_out) {
+  __shared__ uint64_t seg[256];
+  __shared__ uint64_t cur[TW][256];
+  if (threadIdx.x == 0) {
+    uint64_t s = 0;
+    for (int r = 0; r < 256; ++r) { seg[r] = s; s += tot[r]; }
+  }
+  __syncthreads();
+  const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * TW + wl;
+  if (gw >= G_w) return;
+  for (int r = lane; r < 256; r += 32) cur[wl][r] = seg[r] + pre[(uint64_t)gw * 256 + r];
+  __syncwarp();
+  const uint64_t begin = (uint64_t)gw * per_warp, end = min(n, begin + per_warp);
+  const uint32_t lt = (1u << lane) - 1u;
+  for (uint64_t base = begin; base < end; base += 32) {
+    const uint64_t i = base + lane;
+    const bool v = i < end;
+    const K k = v ? key[i] : (K)0;
+    const uint32_t d = v ? ((uint32_t)(k >> shift) & 255u) : 0xFFFFFFFFu;
+    const uint32_t peers = __match_any_sync(TFULL, d);
+    uint64_t pos = 0;
+    if (v) pos = cur[wl][d] + __popc(peers & lt);
+    __syncwarp();
+    if (v && lane == __ffs(peers) - 1) cur[wl][d] += __popc(peers);
+    __syncwarp();
+    if (v) {
+      key_out[pos] = k;
+      idx_out[pos] = idx ? idx[i] : (uint32_t)i;
+    }
+  }
+}
+
+// bitwise OR and AND of all keys: a digit on which they agree needs no pass
+template <typename K>
+__global__ void k_t_bits(const K* key, uint64_t n, unsigned long long* orand) {
+  unsigned long long o = 0, a = ~0ull;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    o |= (unsigned long long)key[i];
+    a &= (unsigned long long)key[i];
+  }
+  for (int d = 16; d > 0; d >>= 1) {
+    o |= __shfl_xor_sync(TFULL, o, d);
+    a &= __shfl_xor_sync(TFULL, a, d);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicOr(&orand[0], o);
+    atomicAnd(&orand[1], a);
+  }
+}
+
+// ------------------------------------------------------------------ segmented scan of maps
+struct TimelineTab {
+  uint64_t maps[RV_MAX_LETTERS];
+  uint8_t labels[RV_MAX_STATES];
+  int n_states, q0, n_letters;
+};
+
+// (a then b) for segment aggregates: b restarts at a head
+__device__ __forceinline__ Agg agg_then(Agg a, Agg b, int ns) {
+  Agg r;
+  r.head = a.head | b.head;
+  r.map = b.head ? b.map : apply_map(a.map, b.map, ns);
+  r.pad = 0;
+  return r;
+}
+
+template <typename K>
+__device__ __forceinline__ bool is_head(const K* key, uint64_t i) {
+  return i == 0 || key[i] != key[i - 1];
+}
+
+// inclusive scan of one aggregate per thread over the CTA; returns the
+// exclusive prefix of this thread, and the CTA total in *total
+__device__ Agg cta_exscan(Agg mine, int ns, Agg* total) {
+  __shared__ Agg wtot[TT / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  Agg incl = mine;
+  for (int d = 1; d < 32; d <<= 1) {
+    Agg y;
+    y.map = __shfl_up_sync(TFULL, incl.map, d);
+    y.head = __shfl_up_sync(TFULL, incl.head, d);
+    if (lane >= d) incl = agg_then(y, incl, ns);
+  }
+  if (lane == 31) wtot[w] = incl;
+  __syncthreads();
+  Agg before{IDENTITY_MAP, 0, 0};
+  for (int v = 0; v < w; ++v) before = agg_then(before, wtot[v], ns);
+  Agg all = before;
+  for (int v = w; v < TT / 32; ++v) all = agg_then(all, wtot[v], ns);
+  Agg ex;
+  ex.map = __shfl_up_sync(TFULL, incl.map, 1);
+  ex.head = __shfl_up_sync(TFULL, incl.head, 1);
+  if (lane == 0) { ex.map = IDENTITY_MAP; ex.head = 0; }
+  *total = all;
+  __syncthreads();
+  return agg_then(before, ex, ns);
+}
+
+template <typename K>
+__device__ __forceinline__ Agg thread_agg(const K* key, const uint32_t* idx, const uint8_t* pred, uint64_t n,
+                                          uint64_t i0, const TimelineTab& tab) {
+  Agg a{IDENTITY_MAP, 0, 0};
+  for (int v = 0; v < TV; ++v) {
+    const uint64_t i = i0 + v;
+    if (i >= n) break;
+    const uint32_t l = pred[idx[i]];
+    const uint64_t m = tab.maps[l < (uint32_t)tab.n_letters ? l : 0];
+    if (is_head(key, i)) { a.head = 1; a.map = m; }
+    else a.map = apply_map(a.map, m, tab.n_states);
+  }
+  return a;
+}
+
+template <typename K>
+__global__ void __launch_bounds__(TT)
+k_t_tiles(const K* key, const uint32_t* idx, const uint8_t* pred, uint64_t n, TimelineTab tab, Agg* tiles,
+          unsigned int* err) {
+  const uint64_t i0 = (uint64_t)blockIdx.x * TTILE + (uint64_t)threadIdx.x * TV;
+  Agg total;
+  const Agg mine = thread_agg(key, idx, pred, n, i0, tab);
+  cta_exscan(mine, tab.n_states, &total);
+  if (threadIdx.x == 0) tiles[blockIdx.x] = total;
+  bool bad = false;
+  for (int v = 0; v < TV; ++v) {
+    const uint64_t i = i0 + v;
+    if (i < n && pred[idx[i]] >= (uint32_t)tab.n_letters) bad = true;
+  }
+  if (__any_sync(TFULL, bad) && (threadIdx.x & 31) == 0) atomicOr(err, (unsigned)ERR_LETTER);
+}
+
+// exclusive scan of the tile aggregates (one CTA, TT per round)
+__global__ void __launch_bounds__(TT) k_t_tilescan(Agg* tiles, uint64_t ntiles, int ns) {
+  __shared__ Agg carry;
+  if (threadIdx.x == 0) carry = Agg{IDENTITY_MAP, 0, 0};
+  __syncthreads();
+  for (uint64_t b = 0; b < ntiles; b += TT) {
+    const uint64_t i = b + threadIdx.x;
+    const Agg mine = i < ntiles ? tiles[i] : Agg{IDENTITY_MAP, 0, 0};
+    Agg total;
+    const Agg ex = cta_exscan(mine, ns, &total);
+    const Agg c = carry;
+    if (i < ntiles) tiles[i] = agg_then(c, ex, ns);
+    __syncthreads();
+    if (threadIdx.x == 0) carry = agg_then(c, total, ns);
+    __syncthreads();
+  }
+}
+
+template <typename K>
+__global__ void __launch_bounds__(TT)
+k_t_emit(const K* key, const uint32_t* idx, const uint8_t* pred, uint64_t n, TimelineTab tab, const Agg* tiles,
+         uint8_t* verdict, uint64_t* vkey, uint32_t* vidx, unsigned long long* nviol) {
+  const uint64_t i0 = (uint64_t)blockIdx.x * TTILE + (uint64_t)threadIdx.x * TV;
+  Agg total;
+  const Agg mine = thread_agg(key, idx, pred, n, i0, tab);
+  const Agg ex = agg_then(tiles[blockIdx.x], cta_exscan(mine, tab.n_states, &total), tab.n_states);
+  // the state before this thread's first event (meaningless if that event is a head)
+  uint32_t q = step_state((uint32_t)tab.q0, ex.map);
+  uint32_t vprev = tab.labels[q];
+  for (int v = 0; v < TV; ++v) {
+    const uint64_t i = i0 + v;
+    if (i >= n) break;
+    const uint32_t j = idx[i];
+    const uint32_t l = pred[j];
+    const uint64_t m = tab.maps[l < (uint32_t)tab.n_letters ? l : 0];
+    const bool head = is_head(key, i);
+    if (head) { q = (uint32_t)tab.q0; vprev = 0xFFu; }
+    q = step_state(q, m);
+    const uint32_t vd = tab.labels[q];
+    verdict[j] = (uint8_t)vd;
+    if (vd == RV_BOT && vprev != RV_BOT) {       // F is permanent: the binding's first F event
+      const unsigned long long slot = atomicAdd(nviol, 1ull);
+      vkey[slot] = (uint64_t)key[i];
+      vidx[slot] = j;
+    }
+    vprev = vd;
+  }
+}
+
+// ------------------------------------------------------------------ host side
+struct TPlan {
+  uint64_t per_warp, ntiles;
+  int G_w;
+  size_t o_k0, o_k1, o_i0, o_i1, o_hist, o_tot, o_tiles, o_orand, o_err, total;
+};
+
+size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+TPlan tplan(uint64_t n, int kbytes) {
+  TPlan p{};
+  const uint64_t max_w = (uint64_t)rv_num_sms() * 3 * TW;
+  const uint64_t gw = std::max<uint64_t>(1, std::min<uint64_t>((n + 2047) / 2048, max_w));
+  p.per_warp = std::max<uint64_t>(32, ((n + gw - 1) / gw + 31) / 32 * 32);
+  p.G_w = (int)std::max<uint64_t>(1, (n + p.per_warp - 1) / p.per_warp);
+  p.ntiles = std::max<uint64_t>(1, (n + TTILE - 1) / TTILE);
+  size_t off = 0;
+  auto take = [&](size_t b) { size_t r = off; off = a256(off + b); return r; };
+  const uint64_t m = std::max<uint64_t>(n, 1);
+  p.o_k0 = take(m * kbytes);
+  p.o_k1 = take(m * kbytes);
+  p.o_i0 = take(m * 4);
+  p.o_i1 = take(m * 4);
+  p.o_hist = take((size_t)p.G_w * 256 * 4);
+  p.o_tot = take(256 * 8);
+  p.o_tiles = take(p.ntiles * sizeof(Agg));
+  p.o_orand = take(16);
+  p.o_err = take(16);
+  p.total = off;
+  return p;
+}
+
+#define TCU(call)                                                                              \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess) return rv_fail(RV_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));  \
+  } while (0)
+
+__global__ void k_t_iota(uint32_t* idx, uint64_t n) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+    idx[i] = (uint32_t)i;
+}
+
+template <typename K>
+__global__ void k_t_const(K* key, uint64_t n) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+    key[i] = 0;
+}
+
+// innermost binding key of every event: the key (one or two variables), or
+// one constant key for an unquantified property
+template <typename K>
+rv_status run_timeline(const rv_formula* f, const rv_trace* t, unsigned char* ws, const TPlan& p, uint8_t* verdict,
+                       uint64_t* vkey, uint32_t* vidx, unsigned long long* nviol, cudaStream_t s) {
+  const uint64_t n = t->n;
+  K* kbuf[2] = {(K*)(ws + p.o_k0), (K*)(ws + p.o_k1)};
+  uint32_t* ibuf[2] = {(uint32_t*)(ws + p.o_i0), (uint32_t*)(ws + p.o_i1)};
+  uint32_t* hist = (uint32_t*)(ws + p.o_hist);
+  uint64_t* tot = (uint64_t*)(ws + p.o_tot);
+  Agg* tiles = (Agg*)(ws + p.o_tiles);
+  unsigned long long* orand = (unsigned long long*)(ws + p.o_orand);
+  unsigned int* err = (unsigned int*)(ws + p.o_err);
+  TCU(cudaMemsetAsync(nviol, 0, 8, s));
+  TCU(cudaMemsetAsync(err, 0, 4, s));
+  const K* key = (const K*)t->key;
+  if (f->n_quant == 0) {              // one binding: the whole trace
+    RV_LAUNCH("k_t_const", k_t_const<K>, 1024, 256, 0, s, kbuf[1], n);
+    key = kbuf[1];
+  }
+  // digits on which every key agrees need no pass
+  const unsigned long long init[2] = {0ull, ~0ull};
+  TCU(cudaMemcpyAsync(orand, init, 16, cudaMemcpyHostToDevice, s));
+  RV_LAUNCH("k_t_bits", k_t_bits<K>, 1024, 256, 0, s, key, n, orand);
+  unsigned long long h_orand[2];
+  TCU(cudaMemcpyAsync(h_orand, orand, 16, cudaMemcpyDeviceToHost, s));
+  TCU(cudaStreamSynchronize(s));
+  const unsigned long long differ = h_orand[0] ^ h_orand[1];
+  const int grid = (p.G_w + TW - 1) / TW;
+  const K* cur_k = key;
+  const uint32_t* cur_i = nullptr;      // identity permutation before the first pass
+  int out = 0;
+  for (int shift = 0; shift < (int)sizeof(K) * 8; shift += 8) {
+    if (((differ >> shift) & 255ull) == 0) continue;
+    RV_LAUNCH("k_t_hist", k_t_hist<K>, grid, TW * 32, 0, s, cur_k, n, p.per_warp, p.G_w, shift, hist);
+    RV_LAUNCH("k_t_colscan", k_t_colscan, 256, 1024, 0, s, hist, p.G_w, tot);
+    RV_LAUNCH("k_t_scatter", k_t_scatter<K>, grid, TW * 32, 0, s, cur_k, cur_i, n, p.per_warp, p.G_w, shift, hist,
+              tot, kbuf[out], ibuf[out]);
+    cur_k = kbuf[out];
+    cur_i = ibuf[out];
+    out ^= 1;
+  }
+  if (!cur_i) {                          // every key equal: the trace order is already grouped
+    RV_LAUNCH("k_t_iota", k_t_iota, 1024, 256, 0, s, ibuf[out], n);
+    cur_i = ibuf[out];
+  }
+  TimelineTab tab;
+  memset(&tab, 0, sizeof tab);
+  for (int l = 0; l < RV_MAX_LETTERS; ++l) tab.maps[l] = l < f->n_letters ? f->maps[l] : IDENTITY_MAP;
+  memcpy(tab.labels, f->labels, sizeof tab.labels);
+  tab.n_states = f->n_states;
+  tab.q0 = f->q0;
+  tab.n_letters = f->n_letters;
+  RV_LAUNCH("k_t_tiles", k_t_tiles<K>, (unsigned)p.ntiles, TT, 0, s, cur_k, cur_i, t->pred, n, tab, tiles, err);
+  RV_LAUNCH("k_t_tilescan", k_t_tilescan, 1, TT, 0, s, tiles, p.ntiles, tab.n_states);
+  RV_LAUNCH("k_t_emit", k_t_emit<K>, (unsigned)p.ntiles, TT, 0, s, cur_k, cur_i, t->pred, n, tab, tiles, verdict,
+            vkey, vidx, nviol);
+  TCU(cudaGetLastError());
+  unsigned int h_err = 0;
+  TCU(cudaMemcpyAsync(&h_err, err, 4, cudaMemcpyDeviceToHost, s));
+  TCU(cudaStreamSynchronize(s));
+  if (h_err & ERR_LETTER) return rv_fail(RV_EINVAL, "predicate code out of range");
+  return RV_OK;
+}
+
+}  // namespace
+
+extern "C" size_t rv_timeline_workspace_size(const rv_formula* f, uint64_t n) {
+  if (!f) return 0;
+  return tplan(n, f->key_bits / 8).total;
+}
+
+extern "C" rv_status rv_verify_timeline(const rv_formula* f, const rv_trace* t, void* ws, size_t ws_bytes,
+                                        uint8_t* event_verdicts, uint64_t* viol_keys, uint32_t* viol_index,
+                                        uint64_t* n_viol, cudaStream_t s) {
+  if (!f || !t || !n_viol) return rv_fail(RV_EINVAL, "null argument");
+  if (t->n > 0xFFFFFFFFull) return rv_fail(RV_EINVAL, "traces are limited to 2^32-1 events");
+  if (t->n && (!t->pred || (f->n_quant && !t->key) || !event_verdicts || !viol_keys || !viol_index || !ws))
+    return rv_fail(RV_EINVAL, "null array");
+  if (t->n == 0) {
+    TCU(cudaMemsetAsync(n_viol, 0, 8, s));
+    TCU(cudaStreamSynchronize(s));
+    return RV_OK;
+  }
+  const TPlan p = tplan(t->n, f->key_bits / 8);
+  if (ws_bytes < p.total) return rv_fail(RV_ENOMEM, "timeline workspace of %zu bytes, need %zu", ws_bytes, p.total);
+  unsigned long long* nv = (unsigned long long*)n_viol;
+  if (f->key_bits == 64)
+    return run_timeline<uint64_t>(f, t, (unsigned char*)ws, p, event_verdicts, viol_keys, viol_index, nv, s);
+  return run_timeline<uint32_t>(f, t, (unsigned char*)ws, p, event_verdicts, viol_keys, viol_index, nv, s);
+}

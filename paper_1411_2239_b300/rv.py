@@ -282,6 +282,35 @@ def parse_result(raw: bytes) -> Result:
     return _result(r)
 
 
+# ---------------------------------------------------------------------- per-event timeline
+def timeline(formula: Formula, key, pred, stream=None):
+    """Per-event verdicts and first violations of a device trace
+    (rv_verify_timeline).  Returns (verdicts: np.uint8[n] in trace order,
+    first_violation: {binding key: event index})."""
+    import torch
+    L = lib()
+    if not getattr(L, "_tl_sigs", False):
+        vp = ctypes.c_void_p
+        L.rv_timeline_workspace_size.argtypes = [vp, ctypes.c_uint64]
+        L.rv_timeline_workspace_size.restype = ctypes.c_size_t
+        L.rv_verify_timeline.argtypes = [vp, ctypes.POINTER(_Trace), vp, ctypes.c_size_t, vp, vp, vp, vp, vp]
+        L._tl_sigs = True
+    n = int(pred.shape[0])
+    dev = pred.device
+    verd = torch.empty(max(n, 1), dtype=torch.uint8, device=dev)
+    vkey = torch.empty(max(n, 1), dtype=torch.int64, device=dev)
+    vidx = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    nv = torch.zeros(1, dtype=torch.int64, device=dev)
+    ws = workspace(int(L.rv_timeline_workspace_size(formula.handle, n)))
+    tr = _Trace(_ptr(key), _ptr(pred), None, n)
+    _check(L.rv_verify_timeline(formula.handle, ctypes.byref(tr), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                _ptr(verd), _ptr(vkey), _ptr(vidx), _ptr(nv), _stream_handle(stream)))
+    k = int(nv.item())
+    keys = vkey[:k].cpu().numpy().view(np.uint64).tolist()
+    idx = vidx[:k].cpu().numpy().view(np.uint32).tolist()
+    return verd[:n].cpu().numpy(), dict(zip(keys, idx))
+
+
 # ---------------------------------------------------------------------- one trace over several ranks
 def _shard_sigs(L):
     if getattr(L, "_shard_sigs", False):
