@@ -1,16 +1,26 @@
 """Throughput benchmark: verified events/s of map -> monitor -> reduce on B300.
 
-    python bench.py [--gpus N --steps K --warmup W] [--workload c2|c1|c3]
+    python bench.py [--gpus N --steps K --warmup W] [--workload c2|c1|c3|c4|c5] [--only]
     python bench.py --impl reference ...      # the CPU oracle on the same workload
 
 A step is one rv_verify_trace of the whole synthetic trace (all stages: key
 multisplit, monitor fold, combine, quantifier reduce) with the trace already
-resident in HBM.  The trace (0.5 GB for the default workload) is larger than
-L2, so no flush is needed between steps.  ``e2e`` repeats the measurement
-through the same C ABI with pinned HOST buffers: the host->device copy of the
-events and the device->host copy of the verdict are inside its timed region.
-Under torchrun every rank verifies its own trace of the same shape (weak
-scaling; no collective on the data path).
+resident in HBM.  The default line is the 1e8-event Zipf socket trace; its
+``workloads`` object adds, measured in the same run, the nested two-variable
+trace, the batched 256 x 32 run (against one launch per trace and formula)
+and the serving run (p50/p99 latency); ``--only`` leaves them out.  Traces
+are larger than L2, so no flush is needed between steps.  ``e2e`` repeats the
+measurement through the same C ABI with pinned HOST buffers: the host->device
+copy of the events and the device->host copy of the verdict are inside its
+timed region.  ``cpu_baseline`` is the oracle on a bounded prefix, on all host
+cores (bindings split over processes) and on one core.
+
+Under torchrun (N > 1) the ranks verify ONE trace of N slices (weak scaling:
+each rank generates a slice of the same size, socket ids disjoint between
+slices): every rank splits its slice by a hash of the socket id
+(rv_shard_trace), an all-to-all exchanges the parts, each rank verifies the
+events of its ids, and an all-reduce of the verdict counts gives the root
+(rv_combine_results).
 """
 from __future__ import annotations
 
@@ -19,6 +29,7 @@ import ctypes
 import hashlib
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -41,18 +52,40 @@ WORKLOADS = {
     "c4": dict(kind="batch", n_traces=256, min_len=1_000, max_len=10_000_000, nf=32, cfg=4),
     # serving: 64 streams of the nested formula, Poisson chunk arrivals
     "c5": dict(kind="serve", formula="A_{>=0.90} u: user(u) => E_{<=3} f: file(u,f) => open && !F close",
-               streams=64, rate=2e8, seconds=10.0, events_per_stream=2_000_000, users=1_600, cfg=5),
+               streams=64, rate=2e8, seconds=8.0, events_per_stream=2_000_000, users=1_600, cfg=5),
 }
 # algorithmic bytes per event: one read of the key and of the predicate byte
 ALG_BYTES = {"c1": 5, "c2": 5, "c3": 9, "c4": 5}
 
 
-def make_trace(w, seed):
+def make_trace(w, seed, ids=None):
     from paper_1411_2239_b300 import synth
     if w["kind"] == "socket":
         return synth.socket_trace(w["n"], w["n_ids"], pending_frac=w.get("pending_frac"),
-                                  n_pending=w.get("n_pending"), zipf_s=w["zipf"], seed=seed)
+                                  n_pending=w.get("n_pending"), zipf_s=w["zipf"], seed=seed, ids=ids)
     return synth.file_trace(w["n"], w["n_users"], w["n_files"], seed=seed)
+
+
+def expected_counts(w, trace):
+    """Root and level counts the generator's construction fixes (socket: the
+    pending ids are exactly the Fp children; file: violating users are Fp
+    outer nodes, the others Tc, leaked pairs Tp inner nodes, the rest F)."""
+    if w["kind"] == "socket":
+        fp = len(trace.meta["pending_ids"])
+        return {"root_counts": [0, 0, fp, trace.meta["appearing"] - fp, 0, 0]}
+    viol = len(trace.meta["violating_users"])
+    leaked, pairs = trace.meta["leaked_pairs"], trace.meta["n_pairs"]
+    outer = [0, 0, viol, 0, trace.meta["n_users"] - viol, 0]
+    return {"root_counts": outer, "level_counts": [outer, [pairs - leaked, 0, 0, leaked, 0, 0]], "root": 4}
+
+
+def matches(res, want):
+    ok = res.status == 0 and res.root_counts == want["root_counts"]
+    if "level_counts" in want:
+        ok &= res.level_counts == want["level_counts"]
+    if "root" in want:
+        ok &= res.root == want["root"]
+    return ok
 
 
 def peaks():
@@ -70,7 +103,7 @@ class Clocks:
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu):
-        self.gpu, self.p, self.path = gpu, None, f"/tmp/rv_clocks_{os.getpid()}.csv"
+        self.gpu, self.p, self.path = gpu, None, f"/tmp/rv_clocks_{os.getpid()}_{gpu}.csv"
 
     def start(self):
         try:
@@ -126,11 +159,42 @@ def traffic_for(kernel, workload):
     return None
 
 
-def cpu_baseline(w, trace, budget_s=20.0):
-    """The oracle, as it stands, on a bounded prefix of the same trace."""
+# ---------------------------------------------------------------------- CPU baseline (the oracle)
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or "unknown"
+
+
+def _oracle_part(job):
+    """Counts of one part of a trace (bindings of a hash class), by the oracle."""
     from oracle.verify import Schema, verify
-    n = 20_000
+    formula, codes, key, pred = job
+    r = verify(formula, Schema(codes), key, pred)
+    nq = len(r.level_counts)
+    return r.root_counts, [r.level_counts[m] if m < nq else [0] * 6 for m in range(2)]
+
+
+def _parts(key, nested, P):
+    outer = (key.astype(np.uint64) >> np.uint64(32)) if nested else key.astype(np.uint64)
+    h = (outer * np.uint64(0x9E3779B97F4A7C15)) >> np.uint64(40)
+    return (h % np.uint64(P)).astype(np.int64)
+
+
+def cpu_baseline(w, trace, budget_s=8.0):
+    """The oracle, as it stands, on a bounded prefix of the same trace: on one
+    core, and on all host cores with the bindings split over processes by a
+    hash of the outer value (the paper's single-core and multi-core arms)."""
+    from oracle.counting import valuate
+    from oracle.formula import parse
+    from oracle.verify import Schema, verify
+    import multiprocessing as mp
     sch = Schema(trace.codes)
+    n = 20_000
     while True:
         t0 = time.perf_counter()
         verify(w["formula"], sch, trace.key[:n], trace.pred[:n])
@@ -138,8 +202,29 @@ def cpu_baseline(w, trace, budget_s=20.0):
         if dt > budget_s / 4 or n >= trace.n:
             break
         n = min(trace.n, int(n * max(2.0, budget_s / 4 / max(dt, 1e-3))))
-    return {"value": n / dt, "unit": "events/s", "cores": 1, "kind": "oracle",
-            "sample": f"first {n} events of the same trace, oracle.verify once ({dt:.1f} s)"}
+    one = {"value": n / dt, "unit": "events/s", "cores": 1,
+           "sample": f"first {n} events of the same trace, oracle.verify once ({dt:.1f} s)"}
+    cores = os.cpu_count() or 1
+    nested = w["kind"] == "file"
+    na = min(trace.n, n * cores)
+    key, pred = trace.key[:na], trace.pred[:na]
+    part = _parts(key, nested, cores)
+    jobs = [(w["formula"], trace.codes, key[part == p], pred[part == p]) for p in range(cores)]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_part, [(w["formula"], trace.codes, key[:10], pred[:10])] * cores)   # start and import
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_part, jobs)
+        dta = time.perf_counter() - t0
+    root_counts = [sum(r[0][v] for r in res) for v in range(6)]
+    root = valuate(parse(w["formula"]).quants[0], root_counts)
+    whole = verify(w["formula"], sch, key, pred) if na <= 4 * n else None
+    agree = None if whole is None else (whole.root == root and whole.root_counts == root_counts)
+    return {"value": na / dta, "unit": "events/s", "cores": cores, "kind": "oracle", "cpu_model": cpu_model(),
+            "nproc": cores,
+            "sample": f"first {na} events of the same trace, bindings split over {cores} processes by a hash of "
+                      f"the outer value, oracle.verify per part ({dta:.1f} s wall)",
+            "parts_agree_with_whole": agree, "one_core": one}
 
 
 def run_reference(args):
@@ -147,6 +232,8 @@ def run_reference(args):
     if rank != 0:
         return
     w = WORKLOADS[args.workload]
+    if w["kind"] not in ("socket", "file"):
+        w = WORKLOADS["c2"]
     trace = make_trace(w, 1000 * w["cfg"] + 0)
     from oracle.verify import Schema, verify
     n = min(trace.n, 200_000)
@@ -164,15 +251,17 @@ def run_reference(args):
             "impl": "reference",
             "config": {"workload": workload_name(args.workload), "events_per_step": n},
             "cpu_baseline": {"value": value, "unit": "events/s", "cores": 1, "kind": "oracle",
+                             "cpu_model": cpu_model(), "nproc": os.cpu_count(),
                              "sample": f"first {n} events of the {args.workload} trace per step"},
             "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
 
+# ---------------------------------------------------------------------- multi-rank pieces
 def combine_ranks(ms, verified, n_local, world):
     """Whole-job numbers from per-rank ones: the step time is the slowest
     rank's, the run is verified only if every rank's is, and the value counts
-    the events of all ranks (weak scaling: each rank has its own trace)."""
+    the events of all ranks (weak scaling: each rank holds its own slice)."""
     if world > 1:
         import torch
         import torch.distributed as dist
@@ -187,53 +276,122 @@ def combine_ranks(ms, verified, n_local, world):
     return ms, verified, n_total / (ms / 1e3)
 
 
+def exchange(key_sorted, pred_sorted, counts):
+    """All-to-all of the events grouped by destination rank: counts[r] events
+    of key_sorted/pred_sorted go to rank r; returns the events this rank
+    receives, in source-rank order (device tensors over NCCL, host ones over
+    gloo)."""
+    import torch
+    import torch.distributed as dist
+    send = [int(x) for x in counts.cpu().tolist()]
+    recv_t = torch.empty_like(counts)
+    dist.all_to_all_single(recv_t, counts)
+    recv = [int(x) for x in recv_t.cpu().tolist()]
+    kout = torch.empty(sum(recv), dtype=key_sorted.dtype, device=key_sorted.device)
+    pout = torch.empty(sum(recv), dtype=pred_sorted.dtype, device=pred_sorted.device)
+    dist.all_to_all_single(kout, key_sorted, recv, send)
+    dist.all_to_all_single(pout, pred_sorted, recv, send)
+    return kout, pout
+
+
+def reduce_result(rv, f, part):
+    """All-reduce of a part's counts, then the root valuated once (rv_combine_results)."""
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    v = torch.tensor(part.root_counts + part.level_counts[0] + part.level_counts[1] + list(part.n_nodes) +
+                     [part.events], dtype=torch.int64, device=dev)
+    dist.all_reduce(v)
+    st = torch.tensor([part.status], dtype=torch.int64, device=dev)
+    dist.all_reduce(st, op=dist.ReduceOp.MAX)
+    v = v.cpu().tolist()
+    summed = rv.Result(0, int(st.item()), v[0:6], [v[6:12], v[12:18]], v[18:20], v[20])
+    return rv.combine_results(f, [summed])
+
+
+def run_sharded(args):
+    """N ranks, one trace of N slices: split, exchange, verify, reduce."""
+    import torch
+    import torch.distributed as dist
+    from paper_1411_2239_b300 import rv
+    world, rank = int(os.environ["WORLD_SIZE"]), int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl")
+    w = WORKLOADS["c2"]
+    # socket ids disjoint between slices: one draw of world * n_ids ids, shared by all ranks
+    ids = np.random.default_rng(1000 * w["cfg"] + 999).choice(np.iinfo(np.uint32).max, size=world * w["n_ids"],
+                                                            replace=False).astype(np.uint32)
+    trace = make_trace(w, 1000 * w["cfg"] + rank, ids=ids[rank * w["n_ids"]:(rank + 1) * w["n_ids"]])
+    f = rv.Formula(w["formula"], trace.codes)
+    key = torch.from_numpy(trace.key.view(np.int32)).cuda()
+    pred = torch.from_numpy(trace.pred).cuda()
+    exp = torch.tensor(expected_counts(w, trace)["root_counts"], dtype=torch.int64, device="cuda")
+    dist.all_reduce(exp)
+    want = exp.cpu().tolist()
+
+    def step():
+        ks, ps, _, counts = rv.shard_trace(f, key, pred, world)
+        kr, pr = exchange(ks, ps, counts)
+        part = rv.verify(f, kr, pr)
+        return reduce_result(rv, f, part)
+
+    for _ in range(args.warmup):
+        res = step()
+    verified = res.status == 0 and res.root_counts == want
+    clk = Clocks(local)
+    clk.start()
+    time.sleep(0.4)
+    dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        res = step()
+    e1.record()
+    torch.cuda.synchronize()
+    dist.barrier()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    verified &= res.root_counts == want
+    ms, verified, value = combine_ranks(ms, verified, trace.n, world)
+    if rank == 0:
+        line = {"metric": "verified events/s", "value": value if verified else 0.0, "unit": "events/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int",
+                "data": "synthetic (seeded; stands in for the paper's Apache/strace case study)",
+                "verified": verified,
+                "config": {"workload": workload_name("c2") + f" per rank, one trace of {world} slices",
+                           "parallelism": f"shard x{world}: split by socket-id hash, all-to-all, all-reduce",
+                           "root_verdict": rv.VERDICT_NAMES[res.root], "l2": "inputs larger than L2 (no flush)"},
+                "clocks": clocks}
+        print(json.dumps(line))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
 def workload_name(k):
     w = WORKLOADS[k]
     if w["kind"] == "socket":
         z = f", Zipf({w['zipf']})" if w["zipf"] else ", uniform"
         return f"{w['formula']} over {w['n']:.0e} events, {w['n_ids']:.0e} socket ids{z}"
-    return f"{w['formula']} over {w['n']:.0e} events, {w['n_users']:.0e} users x {w['n_files']:.0e} files"
+    if w["kind"] == "file":
+        return f"{w['formula']} over {w['n']:.0e} events, {w['n_users']:.0e} users x {w['n_files']:.0e} files"
+    if w["kind"] == "batch":
+        return (f"{w['n_traces']} traces x {w['nf']} formulas, lengths log-uniform in "
+                f"[{w['min_len']:.0e}, {w['max_len']:.0e}]")
+    return (f"{w['streams']} streams, Poisson chunks 4K-1M events at {w['rate']:.0e} events/s offered, "
+            f"{w['seconds']} s, formula of the nested-counting config")
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=list(WORKLOADS))
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--events", type=int, default=0,
-                    help="shrink the workload to about this many events (ids scale with it); profiling only")
-    args = ap.parse_args()
-    if args.events:
-        w = WORKLOADS[args.workload]
-        scale = args.events / w["n"]
-        w["n"] = args.events
-        for k in ("n_ids", "n_users"):
-            if k in w:
-                w[k] = max(10, int(w[k] * scale))
-    if args.impl == "reference":
-        return run_reference(args)
-    if WORKLOADS[args.workload]["kind"] == "batch":
-        return run_batch(args)
-    if WORKLOADS[args.workload]["kind"] == "serve":
-        return run_serve(args)
-
+# ---------------------------------------------------------------------- one trace, one formula
+def bench_offline(args, wname, full=True):
+    """Device throughput of rv_verify_trace_async on one workload; with full,
+    also e2e, per-kernel shares and the CPU baseline."""
     import torch
-    import torch.distributed as dist
     from paper_1411_2239_b300 import rv
-
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl")
-
-    w = WORKLOADS[args.workload]
-    trace = make_trace(w, 1000 * w["cfg"] + rank)
+    w = WORKLOADS[wname]
+    trace = make_trace(w, 1000 * w["cfg"])
     f = rv.Formula(w["formula"], trace.codes, key_bits=w["key_bits"])
     kt = np.uint64 if w["key_bits"] == 64 else np.uint32
     key_np = np.ascontiguousarray(trace.key.astype(kt))
@@ -244,22 +402,18 @@ def main():
     ws = rv.workspace(rv.workspace_size(f, n))
     dres = torch.empty(rv.RESULT_BYTES, dtype=torch.uint8, device="cuda")
 
-    # correctness of this run: the construction's pending sockets are exactly the Fp children
+    # correctness of this run against the generator's construction
     first = rv.verify(f, key, pred)
-    verified = first.status == 0
-    if w["kind"] == "socket":
-        exp_fp = len(trace.meta["pending_ids"])
-        verified &= first.root_counts == [0, 0, exp_fp, trace.meta["appearing"] - exp_fp, 0, 0]
+    want = expected_counts(w, trace)
+    verified = matches(first, want)
 
     for _ in range(args.warmup):
         rv.verify_async(f, key, pred, ws, dres)
     torch.cuda.synchronize()
-    clk = Clocks(local)
+    clk = Clocks(torch.cuda.current_device())
     clk.start()
     time.sleep(0.4)
     launches0 = rv.lib().rv_launch_count()
-    if world > 1:
-        dist.barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -267,14 +421,11 @@ def main():
         rv.verify_async(f, key, pred, ws, dres)
     e1.record(stream)
     torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
     launches = rv.lib().rv_launch_count() - launches0
     clocks = clk.stop()
     ms = e0.elapsed_time(e1) / args.steps
     last = rv.parse_result(bytes(dres.cpu().numpy()))
-    verified &= last.root == first.root and last.root_counts == first.root_counts
-    ms, verified, value = combine_ranks(ms, verified, n, world)
+    verified &= matches(last, want)
 
     # per-kernel durations (CUDA events on the launch stream) over a second timed pass
     rv.lib().rv_profile_enable(1)
@@ -290,16 +441,17 @@ def main():
     top_launches, top_ms = kern[top]
     avg_ms = top_ms / top_launches
     pk, src = peaks()
-    achieved = ALG_BYTES[args.workload] * n / (avg_ms / 1e3) / 1e9
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / pk["hbm_gbs"], "traffic": traffic_for(top, args.workload),
+    alg = ALG_BYTES[wname] * n
+    roofline = {"bound": "hbm", "achieved": alg / (avg_ms / 1e3) / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": alg / (avg_ms / 1e3) / 1e9 / pk["hbm_gbs"], "traffic": traffic_for(top, wname),
                 "kernel": top, "kernel_share": top_ms / prof_total, "peak_source": f"{src} copy bandwidth",
-                "path_achieved": ALG_BYTES[args.workload] * n / (ms / 1e3) / 1e9,
-                "path_frac": ALG_BYTES[args.workload] * n / (ms / 1e3) / 1e9 / pk["hbm_gbs"]}
+                "path_achieved": alg / (ms / 1e3) / 1e9, "path_frac": alg / (ms / 1e3) / 1e9 / pk["hbm_gbs"]}
     kernels = {k: {"launches": v[0], "avg_us": 1e3 * v[1] / v[0], "share": v[1] / prof_total} for k, v in kern.items()}
-
-    e2e = None
-    if not args.no_e2e:
+    out = {"value": n / (ms / 1e3) if verified else 0.0, "unit": "events/s", "ms_per_step": ms, "steps": args.steps,
+           "verified": verified, "events": n, "bindings": int(first.n_nodes[-1 if f.n_quant == 2 else 0]),
+           "root_verdict": rv.VERDICT_NAMES[first.root], "workload": workload_name(wname), "roofline": roofline,
+           "kernels": kernels, "gpu_launches": int(launches), "clocks": clocks}
+    if full and not args.no_e2e:
         kp = torch.empty(key.shape, dtype=key.dtype, pin_memory=True)
         pp = torch.empty(pred.shape, dtype=pred.dtype, pin_memory=True)
         kp.copy_(key.cpu())
@@ -314,28 +466,16 @@ def main():
             r = rv.verify(f, hk, hp)
         torch.cuda.synchronize()
         dt = (time.perf_counter() - t0) / ksteps
-        verified &= r.root == first.root and r.root_counts == first.root_counts
-        e2e = {"value": n / dt, "unit": "events/s", "h2d_bytes_per_step": int(hk.nbytes + hp.nbytes),
-               "d2h_bytes_per_step": rv.RESULT_BYTES, "steps": ksteps}
-
-    if rank != 0:
-        return
-    cpu = None
-    if world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(w, trace)
-    line = {"metric": "verified events/s", "value": value if verified else 0.0, "unit": "events/s",
-            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int",
-            "data": "synthetic (seeded; stands in for the paper's Apache/strace case study)",
-            "verified": verified,
-            "config": {"workload": workload_name(args.workload), "events": n, "bindings": int(first.n_nodes[0]),
-                       "root_verdict": rv.VERDICT_NAMES[first.root], "l2": "inputs larger than L2 (no flush)",
-                       "parallelism": f"weak x{world} (one independent trace per GPU)"},
-            "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": int(launches), "clocks": clocks}
-    print(json.dumps(line))
+        out["verified"] = verified = verified and matches(r, want)
+        out["e2e"] = {"value": n / dt, "unit": "events/s", "h2d_bytes_per_step": int(hk.nbytes + hp.nbytes),
+                      "d2h_bytes_per_step": rv.RESULT_BYTES, "steps": ksteps,
+                      "host_link_gbs": (hk.nbytes + hp.nbytes) / max(dt - ms / 1e3, 1e-9) / 1e9}
+    if full and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(w, trace)
+    return out
 
 
+# ---------------------------------------------------------------------- batched (config 4)
 def formula_pool(rv, rng, n_codes, want, lo=4, hi=16):
     """Random single-quantifier formulas over p0..p{n-1} whose monitors have lo..hi states."""
     from paper_1411_2239_b300 import synth
@@ -354,12 +494,12 @@ def formula_pool(rv, rng, n_codes, want, lo=4, hi=16):
     return out
 
 
-def run_batch(args):
-    """Config 4: one graph replay verifies every (trace, formula) pair; compared
-    with one rv_verify launch per (trace, formula)."""
+def bench_batch(args):
+    """One graph replay verifies every (trace, formula) pair; compared with
+    one rv_verify launch per (trace, formula) on the same device inputs."""
     import torch
     from paper_1411_2239_b300 import rv, synth
-    w = WORKLOADS[args.workload]
+    w = WORKLOADS["c4"]
     traces = synth.batch_traces(w["n_traces"], w["min_len"], w["max_len"], seed=1000 * w["cfg"])
     rng = np.random.default_rng(1000 * w["cfg"] + 1)
     pools = {k: formula_pool(rv, rng, k, 96) for k in range(2, 7)}
@@ -380,7 +520,7 @@ def run_batch(args):
     for _ in range(args.warmup):
         b.run(key, pred, ws, res)
     torch.cuda.synchronize()
-    clk = Clocks(0)
+    clk = Clocks(torch.cuda.current_device())
     clk.start()
     time.sleep(0.3)
     l0 = rv.lib().rv_launch_count()
@@ -407,9 +547,8 @@ def run_batch(args):
     verified = all(r.status == 0 for r in out)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    lanes = 0
-    mism = 0
-    for t, tr in enumerate(traces):
+    lanes = mism = 0
+    for t in range(len(traces)):
         a, z = int(off[t]), int(off[t + 1])
         for j in range(w["nf"]):
             r = rv.verify(forms[t][j], key[a:z], pred[a:z])
@@ -420,21 +559,16 @@ def run_batch(args):
     torch.cuda.synchronize()
     base_s = time.perf_counter() - t0
     verified &= mism == 0
-    value = n / (ms / 1e3)
     pk, src = peaks()
     top = max(kern, key=kern.get) if kern else None
-    line = {"metric": "verified events/s", "value": value if verified else 0.0, "unit": "events/s", "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "int", "data": "synthetic (seeded)",
-            "verified": verified, "config": {"workload": f"{w['n_traces']} traces x {w['nf']} formulas, "
-                                            f"lengths log-uniform in [{w['min_len']:.0e}, {w['max_len']:.0e}], "
-                                            f"{n} events", "autotuned": tuned},
+    return {"value": n / (ms / 1e3) if verified else 0.0, "unit": "events/s", "ms_per_step": ms, "steps": args.steps,
+            "verified": verified, "events": n, "workload": workload_name("c4"), "autotuned": tuned,
             "monitor_steps_per_s": n * w["nf"] / (ms / 1e3),
             "per_launch_baseline": {"seconds_per_batch": base_s, "events_per_s": n / base_s, "launches": lanes,
                                     "mismatches": mism, "speedup_of_batched": base_s / (ms / 1e3)},
-            "roofline": alu_roofline(n * w["nf"], kern, pk, top, ALG_BYTES["c4"] * n / (ms / 1e3) / 1e9 / pk["hbm_gbs"]),
+            "roofline": alu_roofline(n * w["nf"], kern, pk, top,
+                                     ALG_BYTES["c4"] * n / (ms / 1e3) / 1e9 / pk["hbm_gbs"]),
             "kernels_ms": kern, "gpu_launches": int(launches), "clocks": clocks}
-    print(json.dumps(line))
 
 
 def alu_roofline(steps, kern, pk, top, hbm_path_frac):
@@ -443,7 +577,7 @@ def alu_roofline(steps, kern, pk, top, hbm_path_frac):
     instruction per cycle at the maximum SM clock, two instructions per step
     (a table read and a shift-and-mask)."""
     import torch
-    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     peak = sms * 4 * 32 * float(pk.get("sm_max_mhz", 2032.0)) * 1e6 / 2
     fold_ms = kern.get("k_bfold")
     ach = steps / (fold_ms / 1e3) if fold_ms else None
@@ -454,13 +588,13 @@ def alu_roofline(steps, kern, pk, top, hbm_path_frac):
             "hbm_path_frac": hbm_path_frac}
 
 
-def run_serve(args):
-    """Config 5: Poisson chunk arrivals from many streams into one service;
-    throughput and push->verdict latency percentiles."""
+# ---------------------------------------------------------------------- serving (config 5)
+def bench_serve(args):
+    """Poisson chunk arrivals from many streams into one service; throughput
+    and push->verdict latency percentiles."""
     import threading
-    import torch
     from paper_1411_2239_b300 import rv, synth
-    w = WORKLOADS[args.workload]
+    w = WORKLOADS["c5"]
     rng = np.random.default_rng(1000 * w["cfg"])
     codes = synth.FILE_CODES
     streams_data = [synth.file_trace(w["events_per_stream"], w["users"], 1_000_000, seed=1000 * w["cfg"] + i)
@@ -476,6 +610,7 @@ def run_serve(args):
     pos = [0] * w["streams"]
     pushed = [[] for _ in range(w["streams"])]
     lat, got = [], [0] * w["streams"]
+    bad = [0]
     stop = threading.Event()
 
     def poller():
@@ -484,6 +619,7 @@ def run_serve(args):
                 for v in st.poll(256, timeout_us=0):
                     lat.append(v.latency_us)
                     got[i] += 1
+                    bad[0] += v.status != 0
             time.sleep(0.0005)
 
     th = threading.Thread(target=poller, daemon=True)
@@ -519,17 +655,74 @@ def run_serve(args):
     stats = svc.stats()
     svc.close()
     lat_ms = np.array(lat) / 1e3
-    line = {"metric": "verified events/s", "value": stats["events"] / wall, "unit": "events/s", "n_gpus": 1,
-            "steps": int(stats["batches"]), "warmup": 0, "ms_per_step": 1e3 * wall / max(1, stats["batches"]),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int",
-            "data": "synthetic (seeded; streams replay their traces cyclically)",
-            "config": {"workload": f"{w['streams']} streams, Poisson chunks 4K-1M events at {w['rate']:.0e} events/s "
-                                   f"offered, {w['seconds']} s, formula of the nested-counting config"},
-            "offered_events_per_s": events / (t_push_end - t_start), "refused_pushes": refused,
+    return {"value": stats["events"] / wall, "unit": "events/s", "workload": workload_name("c5"),
+            "offered_events_per_s": events / (t_push_end - t_start), "served_events_per_s": stats["events"] / wall,
+            "refused_pushes": refused, "chunks_with_error": int(bad[0]), "batches": int(stats["batches"]),
             "latency_ms": {"p50": float(np.percentile(lat_ms, 50)) if len(lat_ms) else None,
                            "p99": float(np.percentile(lat_ms, 99)) if len(lat_ms) else None,
                            "max": float(lat_ms.max()) if len(lat_ms) else None, "chunks": int(len(lat_ms))},
             "service": stats}
+
+
+# ---------------------------------------------------------------------- main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2", choices=list(WORKLOADS))
+    ap.add_argument("--only", action="store_true", help="the headline workload alone (no workloads object)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--events", type=int, default=0,
+                    help="shrink the workload to about this many events (ids scale with it); profiling only")
+    args = ap.parse_args()
+    if args.events:
+        w = WORKLOADS[args.workload]
+        scale = args.events / w["n"]
+        w["n"] = args.events
+        for k in ("n_ids", "n_users"):
+            if k in w:
+                w[k] = max(10, int(w[k] * scale))
+    if args.impl == "reference":
+        return run_reference(args)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world > 1:
+        return run_sharded(args)
+
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    kind = WORKLOADS[args.workload]["kind"]
+    if kind == "batch":
+        sub = bench_batch(args)
+    elif kind == "serve":
+        sub = bench_serve(args)
+    else:
+        sub = bench_offline(args, args.workload, full=True)
+    line = {"metric": "verified events/s", "value": sub["value"], "unit": "events/s", "n_gpus": 1,
+            "steps": sub.get("steps", args.steps), "warmup": args.warmup,
+            "ms_per_step": sub.get("ms_per_step"), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int",
+            "data": "synthetic (seeded; stands in for the paper's Apache/strace, Dropbox and YouTube case studies)",
+            "verified": sub.get("verified"),
+            "config": {"workload": sub["workload"], "events": sub.get("events"),
+                       "root_verdict": sub.get("root_verdict"), "l2": "inputs larger than L2 (no flush)",
+                       "parallelism": "one GPU"}}
+    for k in ("roofline", "kernels", "cpu_baseline", "e2e", "gpu_launches", "clocks", "latency_ms",
+              "per_launch_baseline", "autotuned"):
+        if k in sub:
+            line[k] = sub[k]
+    if not args.only and args.workload == "c2" and not args.events:
+        line["workloads"] = {}
+        for name, fn in (("c3", lambda: bench_offline(args, "c3", full=False)), ("c4", lambda: bench_batch(args)),
+                         ("c5", lambda: bench_serve(args))):
+            t0 = time.perf_counter()
+            try:
+                line["workloads"][name] = fn()
+            except Exception as e:          # a sub-run's failure is reported, not hidden
+                line["workloads"][name] = {"error": f"{type(e).__name__}: {e}"}
+            line["workloads"][name]["wall_s"] = time.perf_counter() - t0
     print(json.dumps(line))
 
 

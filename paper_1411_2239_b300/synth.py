@@ -63,13 +63,17 @@ def _rank_within_key(key_idx, n_keys):
     return rank, counts, order, starts
 
 
-def socket_trace(n, n_ids, pending_frac=None, n_pending=None, zipf_s=None, seed=0):
+def socket_trace(n, n_ids, pending_frac=None, n_pending=None, zipf_s=None, seed=0, ids=None):
     """Case-study-1-shaped trace (see module docstring).
 
     ``n_pending`` (or ``pending_frac`` of the sockets that appear with at least
-    two events) sockets end with a receive that is never answered."""
+    two events) sockets end with a receive that is never answered.  ``ids``
+    (n_ids distinct uint32) replaces the random socket ids, e.g. to give
+    several slices of one trace disjoint ids."""
     rng = np.random.default_rng(seed)
-    ids = rng.choice(np.iinfo(np.uint32).max, size=n_ids, replace=False).astype(np.uint32)
+    drawn = rng.choice(np.iinfo(np.uint32).max, size=n_ids, replace=False).astype(np.uint32)
+    ids = drawn if ids is None else np.asarray(ids, dtype=np.uint32)
+    assert len(ids) == n_ids
     if zipf_s is None:
         kidx = rng.integers(0, n_ids, size=n, dtype=np.int64)
     else:
