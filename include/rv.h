@@ -63,18 +63,26 @@ enum { RV_LT = 0, RV_LE = 1, RV_GT = 2, RV_GE = 3, RV_EQ = 4 };  /* comparison ~
 
 #define RV_MAX_STATES 16
 #define RV_MAX_LETTERS 256
+#define RV_MAX_CMP 4
 
 /* Interpretation of the predicate byte of an event (Sec. 2: events are sets
  * of predicates).  RV_ONEHOT: code c is the single predicate code_names[c]
  * (n_codes <= 256).  RV_BITMASK: bit i of the byte means code_names[i] holds
  * (n_codes <= 8), so one event can carry several predicates.
  * key_bits: width of the key column, 32 or 64.  With two quantified variables
- * the key must be 64-bit and holds (d0 << 32) | d1. */
+ * the key must be 64-bit and holds (d0 << 32) | d1.
+ * value_name (may be NULL): name of an optional uint32 value column of the
+ * events, a program variable such as case study 2's average chunk size of a
+ * user's session (Sec. 5.1).  Body atoms "value_name ~ c" or
+ * "value_name(args) ~ c" (~ one of < <= > >= =, c an integer constant in
+ * [0, 2^32)) are interpreted predicates: true at an event iff its value
+ * compares so with c. */
 typedef struct {
   int n_codes;
   const char* const* code_names;
   int alphabet;
   int key_bits;
+  const char* value_name;
 } rv_schema;
 
 typedef struct rv_formula rv_formula;
@@ -86,6 +94,8 @@ typedef struct {
   int q0;          /* initial monitor state */
   int key_bits;
   int alphabet;
+  int n_base;      /* letters of the predicate byte alone */
+  int n_cmp;       /* comparison atoms (letter = code + n_base * outcome bits) */
 } rv_formula_info;
 
 /* Parse `text` (Def. 1 syntax, defaults A = A_{=1}, E = E_{>=1}) and
@@ -125,12 +135,15 @@ rv_status rv_valuate(int kind, int op, uint64_t num, uint64_t den, const uint64_
 /* ------------------------------------------------------------------ offline verification */
 
 /* A trace as a structure of arrays in trace order: key (uint32 or uint64 per
- * key_bits), pred (uint8 predicate byte), optional ts (uint32, may be NULL). */
+ * key_bits), pred (uint8 predicate byte), optional ts (uint32, may be NULL),
+ * value (uint32, the schema's value column; needed only by formulas with
+ * comparison atoms, which the offline and timeline entry points accept). */
 typedef struct {
   const void* key;
   const uint8_t* pred;
   const uint32_t* ts;
   uint64_t n;
+  const uint32_t* value;
 } rv_trace;
 
 typedef struct {
@@ -234,8 +247,8 @@ rv_status rv_verify_timeline(const rv_formula* f, const rv_trace* t, void* ws, s
  *   rv_shard_of: the rank of each of n host keys (key_bits of f), written to
  *     the host array rank_out[n].  Host only; no GPU work.
  *   rv_shard_workspace_size / rv_shard_trace: device form.  t holds device
- *     arrays; the events are written to key_out/pred_out (and ts_out when t
- *     has timestamps), device arrays of n entries, grouped into world
+ *     arrays; the events are written to key_out/pred_out (ts_out when t has
+ *     timestamps, value_out when it has values), device arrays of n entries, grouped into world
  *     contiguous segments in rank order, trace order kept inside every
  *     segment; counts_out (device uint64[world]) receives the segment sizes.
  *     ws: device workspace of at least rv_shard_workspace_size bytes.  Work is
@@ -251,8 +264,8 @@ rv_status rv_verify_timeline(const rv_formula* f, const rv_trace* t, void* ws, s
 rv_status rv_shard_of(const rv_formula* f, const void* key, uint64_t n, int world, uint32_t* rank_out);
 size_t rv_shard_workspace_size(uint64_t n, int world);
 rv_status rv_shard_trace(const rv_formula* f, const rv_trace* t, int world, void* ws, size_t ws_bytes,
-                         void* key_out, uint8_t* pred_out, uint32_t* ts_out, uint64_t* counts_out,
-                         cudaStream_t s);
+                         void* key_out, uint8_t* pred_out, uint32_t* ts_out, uint32_t* value_out,
+                         uint64_t* counts_out, cudaStream_t s);
 rv_status rv_combine_results(const rv_formula* f, const rv_result* parts, int n_parts, rv_result* out);
 
 /* ------------------------------------------------------------------ batched verification

@@ -18,7 +18,10 @@ Body grammar (loosest first): ``<->``, ``->`` (right assoc.), ``||``, ``&&``,
 ``U``/``R``/``W`` (right assoc.), unary ``!``/``X``/``F``/``G``, atoms
 ``true``, ``false``, ``name`` or ``name(args)`` (arguments are the bound
 variables and are ignored: within a projected trace u^D the predicate instances
-of the binding hold by construction, Sec. 2.4.3).
+of the binding hold by construction, Sec. 2.4.3), and comparisons
+``name ~ c`` / ``name(args) ~ c`` of the event's value with an integer
+constant (interpreted predicates such as case study 2's
+``avg_chunksize(u) <= maximum``, Sec. 5.1), kept as the atom ``name~c``.
 
 The AST is made of plain tuples so that structurally equal formulas are equal:
   ('true',) ('false',) ('ap', name) ('not', f) ('and', f, g) ('or', f, g)
@@ -208,6 +211,14 @@ class _P:
             self.take()
             if self.peek() == "(":
                 self.args()
+            if self.peek() in OPS:
+                # interpreted predicate: the event's value compared with an
+                # integer constant (case study 2, Sec. 5.1)
+                op = self.take()
+                num = self.take()
+                if not re.fullmatch(r"\d+", num or "") or int(num) > 0xFFFFFFFF:
+                    raise ParseError(f"a comparison needs an integer constant in [0, 2^32), got {num!r}")
+                return ("ap", f"{tok}{op}{int(num)}")
             return ("ap", tok)
         raise ParseError(f"unexpected token {tok!r}")
 

@@ -20,13 +20,14 @@ from .ltl4 import B4_BOT, B4_BOT_P, B4_TOP_P, progress
 from .verify import Checker, Schema, value_vectors
 
 
-def timeline(formula, schema: Schema, keys, preds):
+def timeline(formula, schema: Schema, keys, preds, values=None):
     """(verdicts, first_violation): verdicts[j] is the code (0 F, 2 Fp, 3 Tp,
     5 T) of event j's binding after event j; first_violation maps each
     binding's value vector (a tuple) to the index of its first F event."""
     ck = Checker(formula, schema)
     preds = np.asarray(preds)
     ck.check_preds(preds)
+    preds = ck.letters(preds, values)
     n = len(preds)
     nq = len(ck.formula.quants)
     L = ck.ltl4

@@ -23,6 +23,7 @@ Steps, in the paper's order (Sec. 2.4 and Sec. 3):
 """
 from __future__ import annotations
 
+import re
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -36,6 +37,7 @@ from .ltl4 import LTL4
 class Schema:
     code_names: list          # name of each predicate code
     alphabet: str = "onehot"  # 'onehot' or 'bitmask'
+    value_name: str = None    # name of the events' value column (comparison atoms)
 
     @property
     def n_letters(self):
@@ -77,16 +79,66 @@ def value_vectors(n_vars: int, keys: np.ndarray):
     raise ValueError("at most two quantified variables")
 
 
+_CMP_ATOM = re.compile(r"([A-Za-z]\w*?)(<=|>=|<|>|=)(\d+)")
+_CMP_FN = {"<": lambda v, c: v < c, "<=": lambda v, c: v <= c, ">": lambda v, c: v > c,
+           ">=": lambda v, c: v >= c, "=": lambda v, c: v == c}
+
+
 class Checker:
-    """The formula, schema and LTL4 evaluator of one verification problem."""
+    """The formula, schema and LTL4 evaluator of one verification problem.
+
+    Comparison atoms "name~c" hold at an event iff its value compares so with
+    c.  Each event is then a letter (its predicate code's propositions plus
+    the comparison atoms its value makes true); the letters the trace can
+    produce, over which LTL4 quantifies continuations, are every code with
+    every set of comparison outcomes that some value in [0, 2^32) gives."""
 
     def __init__(self, formula, schema: Schema):
         self.formula: Formula = parse(formula) if isinstance(formula, str) else formula
         self.schema = schema
-        missing = self.formula.aps() - set(schema.code_names)
+        aps = self.formula.aps()
+        self.cmps = sorted(a for a in aps if _CMP_ATOM.fullmatch(a))
+        for a in self.cmps:
+            if _CMP_ATOM.fullmatch(a).group(1) != schema.value_name:
+                raise ValueError(f"comparison atom {a} is not on the schema's value column")
+        missing = aps - set(self.cmps) - set(schema.code_names)
         if missing:
             raise ValueError(f"body propositions not in the schema: {sorted(missing)}")
-        self.ltl4 = LTL4(self.formula.body, letter_sets(schema, self.formula.aps()))
+        base = letter_sets(schema, aps - set(self.cmps))
+        if not self.cmps:
+            self.ltl4 = LTL4(self.formula.body, base)
+            self.ext = None
+            return
+        # outcome sets that some value produces: the atoms are thresholds on one
+        # number, so the values 0, 2^32 - 1 and c - 1, c, c + 1 of every
+        # constant c meet each of them
+        parsed = [_CMP_ATOM.fullmatch(a).groups() for a in self.cmps]
+        cand = {0, 0xFFFFFFFF}
+        for _, _, c in parsed:
+            cand |= {v for v in (int(c) - 1, int(c), int(c) + 1) if 0 <= v <= 0xFFFFFFFF}
+        outcomes = sorted({self._outcome(parsed, v) for v in cand})
+        sets, self.ext = [], {}
+        for code in range(schema.n_letters):
+            for o in outcomes:
+                self.ext[(code, o)] = len(sets)
+                sets.append(frozenset(base[code] | {a for a, on in zip(self.cmps, o) if on}))
+        self._parsed = parsed
+        self.ltl4 = LTL4(self.formula.body, sets)
+
+    @staticmethod
+    def _outcome(parsed, v):
+        return tuple(bool(_CMP_FN[op](v, int(c))) for _, op, c in parsed)
+
+    def letters(self, preds, values):
+        """Letter of every event: its code, with the comparison outcomes of its value."""
+        preds = np.asarray(preds)
+        if self.ext is None:
+            return preds
+        if values is None:
+            raise ValueError("the formula compares the value column: values are needed")
+        values = np.asarray(values)
+        return np.array([self.ext[(int(p), self._outcome(self._parsed, int(v)))] for p, v in zip(preds, values)],
+                        dtype=np.int64)
 
     def check_preds(self, preds):
         preds = np.asarray(preds)
@@ -103,9 +155,10 @@ class Checker:
         mask = np.all(vv == np.asarray(D, dtype=np.uint64).reshape(1, -1), axis=1)
         return np.flatnonzero(mask)
 
-    def run(self, keys, preds) -> Result:
+    def run(self, keys, preds, values=None) -> Result:
         preds = np.asarray(preds)
         self.check_preds(preds)
+        preds = self.letters(preds, values)
         quants = self.formula.quants
         nq = len(quants)
         if nq == 0:
@@ -144,5 +197,5 @@ class Checker:
         return Result(root, list(v), level_counts, n_nodes, verdicts)
 
 
-def verify(formula, schema: Schema, keys, preds) -> Result:
-    return Checker(formula, schema).run(keys, preds)
+def verify(formula, schema: Schema, keys, preds, values=None) -> Result:
+    return Checker(formula, schema).run(keys, preds, values)

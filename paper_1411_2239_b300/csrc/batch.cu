@@ -821,9 +821,10 @@ extern "C" rv_status rv_batch_create(const rv_formula* const* f, int nf, int nt,
   for (int t = 0; t < nt; ++t) {
     for (int j = 0; j < nf; ++j) {
       const rv_formula* F = f[(size_t)t * nf + j];
-      if (!F || F->n_quant != 1 || F->key_bits != 32 || F->n_letters > MAXL) {
+      if (!F || F->n_quant != 1 || F->key_bits != 32 || F->n_letters > MAXL || F->n_cmp) {
         delete b;
-        return rv_fail(RV_EUNSUPPORTED, "batched formulas need one quantifier, 32-bit keys and at most 16 letters");
+        return rv_fail(RV_EUNSUPPORTED, "batched formulas need one quantifier, 32-bit keys, at most 16 letters "
+                                         "and no comparison atoms");
       }
       if (j == 0) b->nletters[t] = (uint32_t)F->n_letters;
       else if (b->nletters[t] != (uint32_t)F->n_letters) {

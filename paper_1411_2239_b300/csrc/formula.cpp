@@ -146,6 +146,8 @@ struct Parser {
   size_t i = 0;
   Builder& B;
   std::vector<std::string> aps;     // distinct body propositions, in order of appearance
+  struct Cmp { std::string name; int op; uint64_t c; };
+  std::vector<Cmp> cmp;             // per proposition: a comparison atom (op >= 0) or a predicate code (op < 0)
   std::vector<rv_quant> quants;
   explicit Parser(Builder& b) : B(b) {}
 
@@ -266,8 +268,23 @@ struct Parser {
     if (p && ident(*p) && *p != "U" && *p != "R" && *p != "W" && *p != "A" && *p != "E") {
       std::string name = take();
       if (at("(")) args();
-      size_t k = std::find(aps.begin(), aps.end(), name) - aps.begin();
-      if (k == aps.size()) aps.push_back(name);
+      int op = -1;
+      uint64_t c = 0;
+      static const char* cmps[] = {"<", "<=", ">", ">=", "="};
+      for (int k = 0; k < 5; ++k)
+        if (at(cmps[k])) op = k;             // RV_LT, RV_LE, RV_GT, RV_GE, RV_EQ in that order
+      std::string atom = name;
+      if (op >= 0) {                         // interpreted predicate: value ~ integer constant
+        take();
+        const std::string num = take();
+        if (num.empty() || !is_digit(num[0]) || num.find('.') != std::string::npos || num.size() > 10)
+          throw ParseFail{RV_EPARSE, "a comparison needs an integer constant, got '" + num + "'"};
+        c = strtoull(num.c_str(), nullptr, 10);
+        if (c > 0xFFFFFFFFull) throw ParseFail{RV_EPARSE, "comparison constant beyond 2^32-1"};
+        atom = name + cmps[op] + std::to_string(c);
+      }
+      size_t k = std::find(aps.begin(), aps.end(), atom) - aps.begin();
+      if (k == aps.size()) { aps.push_back(atom); cmp.push_back(Cmp{name, op, c}); }
       return B.ap((int)k);
     }
     throw ParseFail{RV_EPARSE, std::string("unexpected token '") + (p ? *p : "end") + "'"};
@@ -573,12 +590,25 @@ extern "C" rv_status rv_compile_formula(const char* text, const rv_schema* schem
   if (p.quants.size() == 2 && schema->key_bits != 64)
     return report(rv_fail(RV_EINVAL, "two quantified variables need 64-bit keys (d0 << 32 | d1)"));
   if (p.aps.size() > 64) return report(rv_fail(RV_EUNSUPPORTED, "too many propositions"));
-  std::vector<int> ap_code(p.aps.size(), -1);
+  std::vector<int> ap_code(p.aps.size(), -1), ap_cmp(p.aps.size(), -1);
+  int n_cmp = 0;
   for (size_t a = 0; a < p.aps.size(); ++a) {
+    if (p.cmp[a].op >= 0) {
+      if (!schema->value_name || p.cmp[a].name != schema->value_name)
+        return report(rv_fail(RV_EPARSE, "comparison on '%s', which is not the schema's value column",
+                              p.cmp[a].name.c_str()));
+      if (n_cmp >= RV_MAX_CMP) return report(rv_fail(RV_EUNSUPPORTED, "more than %d comparison atoms", RV_MAX_CMP));
+      ap_cmp[a] = n_cmp++;
+      continue;
+    }
     for (int c = 0; c < schema->n_codes; ++c)
       if (schema->code_names[c] && p.aps[a] == schema->code_names[c]) { ap_code[a] = c; break; }
     if (ap_code[a] < 0) return report(rv_fail(RV_EPARSE, "body proposition '%s' is not a predicate code", p.aps[a].c_str()));
   }
+  const int n_base = schema->alphabet == RV_ONEHOT ? schema->n_codes : (1 << schema->n_codes);
+  if (n_base << n_cmp > RV_MAX_LETTERS)
+    return report(rv_fail(RV_EUNSUPPORTED, "%d predicate letters times %d comparison outcomes exceed %d letters",
+                          n_base, 1 << n_cmp, RV_MAX_LETTERS));
   rv_formula* f = new (std::nothrow) rv_formula();
   if (!f) return report(rv_fail(RV_ENOMEM, "out of host memory"));
   f->n_quant = (int)p.quants.size();
@@ -586,14 +616,48 @@ extern "C" rv_status rv_compile_formula(const char* text, const rv_schema* schem
   f->key_bits = schema->key_bits;
   f->alphabet = schema->alphabet;
   f->n_codes = schema->n_codes;
-  f->n_letters = schema->alphabet == RV_ONEHOT ? schema->n_codes : (1 << schema->n_codes);
+  f->n_base = n_base;
+  f->n_cmp = n_cmp;
+  for (size_t a = 0; a < p.aps.size(); ++a)
+    if (ap_cmp[a] >= 0) { f->cmp_op[ap_cmp[a]] = p.cmp[a].op; f->cmp_c[ap_cmp[a]] = (uint32_t)p.cmp[a].c; }
+  f->n_letters = n_base << n_cmp;
   f->text = text;
+  // comparison outcomes some value can produce: the atoms are thresholds on one
+  // variable, so the values 0, 2^32-1 and c-1, c, c+1 of every constant meet
+  // every outcome there is
+  std::vector<char> realisable((size_t)1 << n_cmp, 0);
+  {
+    std::vector<uint64_t> cand{0ull, 0xFFFFFFFFull};
+    for (int j = 0; j < n_cmp; ++j)
+      for (int d = -1; d <= 1; ++d) {
+        const int64_t v = (int64_t)f->cmp_c[j] + d;
+        if (v >= 0 && v <= 0xFFFFFFFFll) cand.push_back((uint64_t)v);
+      }
+    for (uint64_t v : cand) {
+      unsigned bits = 0;
+      for (int j = 0; j < n_cmp; ++j) {
+        const uint64_t c = f->cmp_c[j];
+        const int op = f->cmp_op[j];
+        const bool on = op == RV_LT ? v < c : op == RV_LE ? v <= c : op == RV_GT ? v > c : op == RV_GE ? v >= c : v == c;
+        if (on) bits |= 1u << j;
+      }
+      realisable[bits] = 1;
+    }
+  }
+  unsigned first_real = 0;
+  while (!realisable[first_real]) ++first_real;
   std::vector<uint64_t> mask(f->n_letters, 0);
-  for (int l = 0; l < f->n_letters; ++l)
+  for (int l = 0; l < f->n_letters; ++l) {
+    const int base = l % n_base;
+    unsigned bits = (unsigned)(l / n_base);
+    if (!realisable[bits]) bits = first_real;   // never produced; kept out of the effective alphabet
     for (size_t a = 0; a < p.aps.size(); ++a) {
-      bool on = schema->alphabet == RV_ONEHOT ? (ap_code[a] == l) : ((l >> ap_code[a]) & 1);
+      bool on;
+      if (ap_cmp[a] >= 0) on = (bits >> ap_cmp[a]) & 1u;
+      else on = schema->alphabet == RV_ONEHOT ? (ap_code[a] == base) : ((base >> ap_code[a]) & 1);
       if (on) mask[l] |= 1ull << a;
     }
+  }
   rv_status st;
   try {
     st = synthesise(B, root, mask, f);
@@ -613,6 +677,8 @@ extern "C" rv_status rv_formula_get_info(const rv_formula* f, rv_formula_info* i
   info->q0 = f->q0;
   info->key_bits = f->key_bits;
   info->alphabet = f->alphabet;
+  info->n_base = f->n_base;
+  info->n_cmp = f->n_cmp;
   return RV_OK;
 }
 

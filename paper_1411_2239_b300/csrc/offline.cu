@@ -2049,7 +2049,8 @@ struct Plan {
   // workspace offsets
   size_t o_acc, o_hist, o_part, o_tot1, o_bstart1, o_recA, o_recB, o_tiles2, o_tf2, o_tk2, o_hist2, o_ssum2,
       o_bstart2, o_units, o_uf, o_uk, o_items0, o_items1, o_groups, o_gf0, o_gk0, o_gf1, o_gk1, o_pool0,
-      o_pool1, o_res, o_hkey, o_hpred, o_hts, o_uend, o_htk, o_htc, o_hcnt, o_hlist, o_mids, o_mk, o_mf, total;
+      o_pool1, o_res, o_hkey, o_hpred, o_hts, o_uend, o_htk, o_htc, o_hcnt, o_hlist, o_mids, o_mk, o_mf, o_letters,
+      o_hval, total;
 };
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -2146,6 +2147,8 @@ static Plan make_plan(const rv_formula* f, uint64_t n, int host_input, const rv_
   pl.o_hkey = host_input ? take(n * (f->key_bits / 8)) : 0;
   pl.o_hpred = host_input ? take(n) : 0;
   pl.o_hts = host_input ? take(n * 4) : 0;
+  pl.o_letters = f->n_cmp ? take(std::max<uint64_t>(n, 1)) : 0;
+  pl.o_hval = host_input && f->n_cmp ? take(n * 4) : 0;
   pl.total = off;
   return pl;
 }
@@ -2173,10 +2176,17 @@ static MonitorTab make_tab(const rv_formula* f) {
 template <int F>
 static rv_status launch_all(const Plan& pl, const rv_formula* f, const void* key, const uint8_t* pred,
                             const uint32_t* ts, unsigned char* ws, rv_result* dev_out, const rv_bindings* b,
-                            cudaStream_t s, const StreamState* ss = nullptr) {
+                            cudaStream_t s, const StreamState* ss = nullptr, const uint32_t* value = nullptr) {
   typedef typename RecT<F>::type Rec;
   Acc* acc = (Acc*)(ws + pl.o_acc);
   RV_CU(cudaMemsetAsync(acc, 0, sizeof(Acc), s));
+  if (f->n_cmp && pl.n) {              // comparison atoms: fold each event's value into its letter
+    uint8_t* letters = ws + pl.o_letters;
+    const unsigned g = (unsigned)std::min<uint64_t>((pl.n + 255) / 256, (uint64_t)num_sms() * 8);
+    RV_LAUNCH("k_cmp_letters", k_cmp_letters, g, 256, 0, s, pred, value, pl.n, cmp_tab(f), letters, &acc->err,
+              (unsigned)ERR_LETTER);
+    pred = letters;
+  }
   Params p;
   memset(&p, 0, sizeof p);
   p.tab = make_tab(f);
@@ -2323,12 +2333,12 @@ static rv_status set_attrs() {
 
 static rv_status dispatch(const Plan& pl, const rv_formula* f, const void* key, const uint8_t* pred, const uint32_t* ts,
                           unsigned char* ws, rv_result* dev_out, const rv_bindings* b, cudaStream_t s,
-                          const StreamState* ss = nullptr) {
+                          const StreamState* ss = nullptr, const uint32_t* value = nullptr) {
   rv_status st;
   switch (pl.F) {
-    case FMT_K32: st = set_attrs<FMT_K32>(); if (st) return st; return launch_all<FMT_K32>(pl, f, key, pred, ts, ws, dev_out, b, s, ss);
-    case FMT_K64: st = set_attrs<FMT_K64>(); if (st) return st; return launch_all<FMT_K64>(pl, f, key, pred, ts, ws, dev_out, b, s, ss);
-    default: st = set_attrs<FMT_K2>(); if (st) return st; return launch_all<FMT_K2>(pl, f, key, pred, ts, ws, dev_out, b, s, ss);
+    case FMT_K32: st = set_attrs<FMT_K32>(); if (st) return st; return launch_all<FMT_K32>(pl, f, key, pred, ts, ws, dev_out, b, s, ss, value);
+    case FMT_K64: st = set_attrs<FMT_K64>(); if (st) return st; return launch_all<FMT_K64>(pl, f, key, pred, ts, ws, dev_out, b, s, ss, value);
+    default: st = set_attrs<FMT_K2>(); if (st) return st; return launch_all<FMT_K2>(pl, f, key, pred, ts, ws, dev_out, b, s, ss, value);
   }
 }
 
@@ -2391,6 +2401,8 @@ static rv_status check_args(const rv_formula* f, const rv_trace* t) {
   if (t->n > 0xFFFFFFFFull) return rv_fail(RV_EINVAL, "traces are limited to 2^32-1 events");
   if (t->n && (!t->key || !t->pred)) return rv_fail(RV_EINVAL, "null key or pred array");
   if (f->n_quant == 0 && t->n == 0) return rv_fail(RV_EINVAL, "an unquantified property needs a non-empty trace");
+  if (f->n_cmp && t->n && !t->value)
+    return rv_fail(RV_EINVAL, "the formula compares the value column: the trace needs its value array");
   return RV_OK;
 }
 
@@ -2402,7 +2414,7 @@ extern "C" rv_status rv_verify_trace_async(const rv_formula* f, const rv_trace* 
   if (!ws || !dev_out) return rv_fail(RV_EINVAL, "the asynchronous form needs a workspace and a device result");
   Plan pl = make_plan(f, t->n, 0, opts, 0);
   if (ws_bytes < pl.total) return rv_fail(RV_ENOMEM, "workspace of %zu bytes, need %zu", ws_bytes, pl.total);
-  return dispatch(pl, f, t->key, t->pred, t->ts, (unsigned char*)ws, dev_out, bindings, s);
+  return dispatch(pl, f, t->key, t->pred, t->ts, (unsigned char*)ws, dev_out, bindings, s, nullptr, t->value);
 }
 
 extern "C" rv_status rv_verify_trace(const rv_formula* f, const rv_trace* t, int on_device, void* ws, size_t ws_bytes,
@@ -2428,19 +2440,22 @@ extern "C" rv_status rv_verify_trace(const rv_formula* f, const rv_trace* t, int
     const void* key = t->key;
     const uint8_t* pred = t->pred;
     const uint32_t* ts = t->ts;
+    const uint32_t* value = t->value;
     st = RV_OK;
     if (!on_device && t->n) {
       const size_t kb = (size_t)t->n * (f->key_bits / 8);
       if (cudaMemcpyAsync(w + pl.o_hkey, t->key, kb, cudaMemcpyHostToDevice, s) != cudaSuccess ||
           cudaMemcpyAsync(w + pl.o_hpred, t->pred, t->n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-          (t->ts && cudaMemcpyAsync(w + pl.o_hts, t->ts, t->n * 4, cudaMemcpyHostToDevice, s) != cudaSuccess))
+          (t->ts && cudaMemcpyAsync(w + pl.o_hts, t->ts, t->n * 4, cudaMemcpyHostToDevice, s) != cudaSuccess) ||
+          (f->n_cmp && cudaMemcpyAsync(w + pl.o_hval, t->value, t->n * 4, cudaMemcpyHostToDevice, s) != cudaSuccess))
         st = rv_fail(RV_ECUDA, "host-to-device copy failed");
       key = w + pl.o_hkey;
       pred = w + pl.o_hpred;
       ts = t->ts ? (const uint32_t*)(w + pl.o_hts) : nullptr;
+      value = f->n_cmp ? (const uint32_t*)(w + pl.o_hval) : nullptr;
     }
     rv_result* dres = (rv_result*)(w + pl.o_res);
-    if (!st) st = dispatch(pl, f, key, pred, ts, w, dres, bindings, s);
+    if (!st) st = dispatch(pl, f, key, pred, ts, w, dres, bindings, s, nullptr, value);
     if (!st && cudaMemcpyAsync(pinned, dres, sizeof(rv_result), cudaMemcpyDeviceToHost, s) != cudaSuccess)
       st = rv_fail(RV_ECUDA, "device-to-host copy failed");
     cudaError_t e = cudaStreamSynchronize(s);

@@ -169,6 +169,49 @@ struct MonitorTab {
   rv_quant q[2];
 };
 
+// ------------------------------------------------------------------ interpreted comparison atoms
+// Body atoms "value ~ c" are folded into the letter at ingest: letter =
+// code + n_base * (bit j set iff atom j holds for the event's value).
+struct CmpTab {
+  int n_base, n_cmp;
+  int op[RV_MAX_CMP];
+  uint32_t c[RV_MAX_CMP];
+};
+
+inline CmpTab cmp_tab(const rv_formula* f) {
+  CmpTab t;
+  t.n_base = f->n_base;
+  t.n_cmp = f->n_cmp;
+  for (int j = 0; j < RV_MAX_CMP; ++j) { t.op[j] = f->cmp_op[j]; t.c[j] = f->cmp_c[j]; }
+  return t;
+}
+
+__device__ __forceinline__ uint32_t cmp_bits(const CmpTab& t, uint32_t v) {
+  uint32_t bits = 0;
+#pragma unroll
+  for (int j = 0; j < RV_MAX_CMP; ++j) {
+    if (j >= t.n_cmp) break;
+    const uint32_t c = t.c[j];
+    const int op = t.op[j];
+    const bool on = op == RV_LT ? v < c : op == RV_LE ? v <= c : op == RV_GT ? v > c : op == RV_GE ? v >= c : v == c;
+    bits |= (uint32_t)on << j;
+  }
+  return bits;
+}
+
+// letters of n events from their predicate codes and values; a code outside
+// the schema sets `bad_bit` in *err (the letter is then 0)
+static __global__ void k_cmp_letters(const uint8_t* pred, const uint32_t* value, uint64_t n, CmpTab t,
+                                     uint8_t* out, unsigned int* err, unsigned int bad_bit) {
+  bool bad = false;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t code = pred[i];
+    if (code >= (uint32_t)t.n_base) { bad = true; out[i] = 0; continue; }
+    out[i] = (uint8_t)(code + (uint32_t)t.n_base * cmp_bits(t, value[i]));
+  }
+  if (__any_sync(0xFFFFFFFFu, bad) && (threadIdx.x & 31) == 0) atomicOr(err, bad_bit);
+}
+
 // ------------------------------------------------------------------ accumulators of one verification
 enum {
   ERR_LETTER = 1,       // predicate byte out of range

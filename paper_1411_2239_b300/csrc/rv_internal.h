@@ -21,6 +21,11 @@ struct rv_formula {
   int n_letters;
   int n_states;
   int q0;
+  // comparison atoms "value ~ c" of the body: letter = code + n_base * (bit j: atom j holds)
+  int n_base;                      // letters of the predicate byte alone (n_codes or 2^n_codes)
+  int n_cmp;
+  int cmp_op[RV_MAX_CMP];          // RV_LT .. RV_EQ
+  uint32_t cmp_c[RV_MAX_CMP];
   uint64_t maps[RV_MAX_LETTERS];   // nibble s of maps[l] = delta(s, l)
   uint8_t labels[RV_MAX_STATES];   // lambda(s) as rv_verdict code
   std::string text;

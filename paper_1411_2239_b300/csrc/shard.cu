@@ -94,9 +94,9 @@ __global__ void __launch_bounds__(1024) k_shard_scan(uint32_t* hist, int G_w, in
 // exclusive prefix inside the destination rank's segment
 template <typename K>
 __global__ void __launch_bounds__(SH_THREADS)
-k_shard_scatter(const K* key, const uint8_t* pred, const uint32_t* ts, uint64_t n, uint64_t per_warp, int G_w,
-                int shift, int world, const uint32_t* pre, const uint64_t* counts, K* key_out, uint8_t* pred_out,
-                uint32_t* ts_out) {
+k_shard_scatter(const K* key, const uint8_t* pred, const uint32_t* ts, const uint32_t* value, uint64_t n,
+                uint64_t per_warp, int G_w, int shift, int world, const uint32_t* pre, const uint64_t* counts,
+                K* key_out, uint8_t* pred_out, uint32_t* ts_out, uint32_t* value_out) {
   __shared__ uint64_t seg[SH_MAX_WORLD];
   __shared__ uint64_t cur[SH_WARPS][SH_MAX_WORLD];
   if (threadIdx.x == 0) {
@@ -125,6 +125,7 @@ k_shard_scatter(const K* key, const uint8_t* pred, const uint32_t* ts, uint64_t 
       key_out[pos] = key[i];
       pred_out[pos] = pred[i];
       if (ts_out) ts_out[pos] = ts[i];
+      if (value_out) value_out[pos] = value[i];
     }
   }
 }
@@ -158,14 +159,15 @@ rv_status check_world(const rv_formula* f, int world) {
 
 template <typename K>
 rv_status launch_shard(const rv_trace* t, int world, int shift, unsigned char* ws, const ShardPlan& p, K* key_out,
-                       uint8_t* pred_out, uint32_t* ts_out, uint64_t* counts, cudaStream_t s) {
+                       uint8_t* pred_out, uint32_t* ts_out, uint32_t* value_out, uint64_t* counts, cudaStream_t s) {
   uint32_t* hist = (uint32_t*)(ws + p.o_hist);
   const int grid = (p.G_w + SH_WARPS - 1) / SH_WARPS;
   const K* key = (const K*)t->key;
   RV_LAUNCH("k_shard_hist", k_shard_hist<K>, grid, SH_THREADS, 0, s, key, t->n, p.per_warp, p.G_w, shift, world, hist);
   RV_LAUNCH("k_shard_scan", k_shard_scan, world, 1024, 0, s, hist, p.G_w, world, counts);
-  RV_LAUNCH("k_shard_scatter", k_shard_scatter<K>, grid, SH_THREADS, 0, s, key, t->pred, t->ts, t->n, p.per_warp,
-            p.G_w, shift, world, hist, counts, key_out, pred_out, t->ts ? ts_out : nullptr);
+  RV_LAUNCH("k_shard_scatter", k_shard_scatter<K>, grid, SH_THREADS, 0, s, key, t->pred, t->ts, t->value, t->n,
+            p.per_warp, p.G_w, shift, world, hist, counts, key_out, pred_out, t->ts ? ts_out : nullptr,
+            t->value ? value_out : nullptr);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return rv_fail(RV_ECUDA, "shard launch: %s", cudaGetErrorString(e));
   return RV_OK;
@@ -179,13 +181,14 @@ extern "C" size_t rv_shard_workspace_size(uint64_t n, int world) {
 }
 
 extern "C" rv_status rv_shard_trace(const rv_formula* f, const rv_trace* t, int world, void* ws, size_t ws_bytes,
-                                    void* key_out, uint8_t* pred_out, uint32_t* ts_out, uint64_t* counts_out,
-                                    cudaStream_t s) {
+                                    void* key_out, uint8_t* pred_out, uint32_t* ts_out, uint32_t* value_out,
+                                    uint64_t* counts_out, cudaStream_t s) {
   if (rv_status st = check_world(f, world)) return st;
   if (!t || !counts_out) return rv_fail(RV_EINVAL, "null trace or counts");
   if (t->n && (!t->key || !t->pred || !key_out || !pred_out || !ws))
     return rv_fail(RV_EINVAL, "null key, pred, output or workspace");
   if (t->n && t->ts && !ts_out) return rv_fail(RV_EINVAL, "the trace has timestamps: ts_out is needed");
+  if (t->n && t->value && !value_out) return rv_fail(RV_EINVAL, "the trace has values: value_out is needed");
   if (t->n > 0xFFFFFFFFull) return rv_fail(RV_EINVAL, "traces are limited to 2^32-1 events");
   if (t->n == 0) {
     const cudaError_t e = cudaMemsetAsync(counts_out, 0, (size_t)world * 8, s);
@@ -196,9 +199,9 @@ extern "C" rv_status rv_shard_trace(const rv_formula* f, const rv_trace* t, int 
   const int shift = f->n_quant == 2 ? 32 : 0;
   if (f->key_bits == 64)
     return launch_shard<uint64_t>(t, world, shift, (unsigned char*)ws, p, (uint64_t*)key_out, pred_out, ts_out,
-                                  counts_out, s);
+                                  value_out, counts_out, s);
   return launch_shard<uint32_t>(t, world, shift, (unsigned char*)ws, p, (uint32_t*)key_out, pred_out, ts_out,
-                                counts_out, s);
+                                value_out, counts_out, s);
 }
 
 extern "C" rv_status rv_shard_of(const rv_formula* f, const void* key, uint64_t n, int world, uint32_t* rank_out) {

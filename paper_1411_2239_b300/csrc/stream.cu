@@ -548,6 +548,7 @@ extern "C" rv_status rv_service_open(const rv_formula* f, const rv_service_cfg* 
   *out = nullptr;
   if (f->n_quant < 1 || f->n_quant > 2) return rv_fail(RV_EUNSUPPORTED, "streaming needs one or two quantifiers");
   if (f->n_quant == 1 && f->key_bits != 32) return rv_fail(RV_EUNSUPPORTED, "one-quantifier streams use 32-bit keys");
+  if (f->n_cmp) return rv_fail(RV_EUNSUPPORTED, "streams carry no value column: no comparison atoms");
   rv_service* S = new (std::nothrow) rv_service();
   if (!S) return rv_fail(RV_ENOMEM, "out of host memory");
   S->f = *f;

@@ -277,7 +277,7 @@ k_t_emit(const K* key, const uint32_t* idx, const uint8_t* pred, uint64_t n, Tim
 struct TPlan {
   uint64_t per_warp, ntiles;
   int G_w;
-  size_t o_k0, o_k1, o_i0, o_i1, o_hist, o_tot, o_tiles, o_orand, o_err, total;
+  size_t o_k0, o_k1, o_i0, o_i1, o_hist, o_tot, o_tiles, o_orand, o_err, o_letters, total;
 };
 
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -301,6 +301,7 @@ TPlan tplan(uint64_t n, int kbytes) {
   p.o_tiles = take(p.ntiles * sizeof(Agg));
   p.o_orand = take(16);
   p.o_err = take(16);
+  p.o_letters = take(m);
   p.total = off;
   return p;
 }
@@ -337,6 +338,13 @@ rv_status run_timeline(const rv_formula* f, const rv_trace* t, unsigned char* ws
   unsigned int* err = (unsigned int*)(ws + p.o_err);
   TCU(cudaMemsetAsync(nviol, 0, 8, s));
   TCU(cudaMemsetAsync(err, 0, 4, s));
+  const uint8_t* pred = t->pred;
+  if (f->n_cmp) {                     // comparison atoms: fold each event's value into its letter
+    uint8_t* letters = ws + p.o_letters;
+    RV_LAUNCH("k_cmp_letters", k_cmp_letters, 1024, 256, 0, s, pred, t->value, n, cmp_tab(f), letters, err,
+              (unsigned)ERR_LETTER);
+    pred = letters;
+  }
   const K* key = (const K*)t->key;
   if (f->n_quant == 0) {              // one binding: the whole trace
     RV_LAUNCH("k_t_const", k_t_const<K>, 1024, 256, 0, s, kbuf[1], n);
@@ -375,9 +383,9 @@ rv_status run_timeline(const rv_formula* f, const rv_trace* t, unsigned char* ws
   tab.n_states = f->n_states;
   tab.q0 = f->q0;
   tab.n_letters = f->n_letters;
-  RV_LAUNCH("k_t_tiles", k_t_tiles<K>, (unsigned)p.ntiles, TT, 0, s, cur_k, cur_i, t->pred, n, tab, tiles, err);
+  RV_LAUNCH("k_t_tiles", k_t_tiles<K>, (unsigned)p.ntiles, TT, 0, s, cur_k, cur_i, pred, n, tab, tiles, err);
   RV_LAUNCH("k_t_tilescan", k_t_tilescan, 1, TT, 0, s, tiles, p.ntiles, tab.n_states);
-  RV_LAUNCH("k_t_emit", k_t_emit<K>, (unsigned)p.ntiles, TT, 0, s, cur_k, cur_i, t->pred, n, tab, tiles, verdict,
+  RV_LAUNCH("k_t_emit", k_t_emit<K>, (unsigned)p.ntiles, TT, 0, s, cur_k, cur_i, pred, n, tab, tiles, verdict,
             vkey, vidx, nviol);
   TCU(cudaGetLastError());
   unsigned int h_err = 0;
@@ -401,6 +409,8 @@ extern "C" rv_status rv_verify_timeline(const rv_formula* f, const rv_trace* t, 
   if (t->n > 0xFFFFFFFFull) return rv_fail(RV_EINVAL, "traces are limited to 2^32-1 events");
   if (t->n && (!t->pred || (f->n_quant && !t->key) || !event_verdicts || !viol_keys || !viol_index || !ws))
     return rv_fail(RV_EINVAL, "null array");
+  if (t->n && f->n_cmp && !t->value)
+    return rv_fail(RV_EINVAL, "the formula compares the value column: the trace needs its value array");
   if (t->n == 0) {
     TCU(cudaMemsetAsync(n_viol, 0, 8, s));
     TCU(cudaStreamSynchronize(s));

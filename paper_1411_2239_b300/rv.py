@@ -34,15 +34,17 @@ class RVError(RuntimeError):
 
 class _Schema(ctypes.Structure):
     _fields_ = [("n_codes", ctypes.c_int), ("code_names", ctypes.POINTER(ctypes.c_char_p)),
-                ("alphabet", ctypes.c_int), ("key_bits", ctypes.c_int)]
+                ("alphabet", ctypes.c_int), ("key_bits", ctypes.c_int), ("value_name", ctypes.c_char_p)]
 
 
 class _Info(ctypes.Structure):
-    _fields_ = [(n, ctypes.c_int) for n in ("n_quant", "n_states", "n_letters", "q0", "key_bits", "alphabet")]
+    _fields_ = [(n, ctypes.c_int) for n in ("n_quant", "n_states", "n_letters", "q0", "key_bits", "alphabet",
+                                            "n_base", "n_cmp")]
 
 
 class _Trace(ctypes.Structure):
-    _fields_ = [("key", ctypes.c_void_p), ("pred", ctypes.c_void_p), ("ts", ctypes.c_void_p), ("n", ctypes.c_uint64)]
+    _fields_ = [("key", ctypes.c_void_p), ("pred", ctypes.c_void_p), ("ts", ctypes.c_void_p), ("n", ctypes.c_uint64),
+                ("value", ctypes.c_void_p)]
 
 
 class _Result(ctypes.Structure):
@@ -114,13 +116,14 @@ class Quantifier:
 class Formula:
     """A compiled LTL4-C formula (owns an rv_formula)."""
 
-    def __init__(self, text: str, codes, alphabet: str = "onehot", key_bits: int = 32):
+    def __init__(self, text: str, codes, alphabet: str = "onehot", key_bits: int = 32, value_name=None):
         L = lib()
         self.text, self.codes = text, list(codes)
         self.alphabet = ONEHOT if alphabet == "onehot" else BITMASK
         names = (ctypes.c_char_p * len(self.codes))(*[c.encode() for c in self.codes])
         self._names = names
-        sch = _Schema(len(self.codes), names, self.alphabet, key_bits)
+        self._value_name = None if value_name is None else value_name.encode()
+        sch = _Schema(len(self.codes), names, self.alphabet, key_bits, self._value_name)
         h = ctypes.c_void_p()
         err = ctypes.create_string_buffer(512)
         st = L.rv_compile_formula(text.encode(), ctypes.byref(sch), ctypes.byref(h), err, 512)
@@ -131,6 +134,7 @@ class Formula:
         _check(L.rv_formula_get_info(h, ctypes.byref(info)))
         self.n_quant, self.n_states, self.n_letters = info.n_quant, info.n_states, info.n_letters
         self.q0, self.key_bits = info.q0, info.key_bits
+        self.n_base, self.n_cmp = info.n_base, info.n_cmp
 
     @property
     def handle(self):
@@ -221,20 +225,22 @@ def _stream_handle(stream):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def verify(formula: Formula, key, pred, ts=None, stream=None, want_bindings=False, opts=None, ws=None) -> Result:
-    """Verify one trace.  key/pred/ts: torch CUDA tensors (device path) or
-    NumPy arrays (host path: copied in by the library)."""
+def verify(formula: Formula, key, pred, ts=None, stream=None, want_bindings=False, opts=None, ws=None,
+           value=None) -> Result:
+    """Verify one trace.  key/pred/ts/value: torch CUDA tensors (device path)
+    or NumPy arrays (host path: copied in by the library)."""
     import torch
     on_device = isinstance(pred, torch.Tensor) and pred.is_cuda
     if not on_device:
         key = np.ascontiguousarray(key)
         pred = np.ascontiguousarray(pred, dtype=np.uint8)
         ts = None if ts is None else np.ascontiguousarray(ts, dtype=np.uint32)
+        value = None if value is None else np.ascontiguousarray(value, dtype=np.uint32)
         want_kb = 8 if formula.key_bits == 64 else 4
         if key.dtype.itemsize != want_kb:
             key = key.astype(np.uint64 if want_kb == 8 else np.uint32)
     n = int(pred.shape[0])
-    tr = _Trace(_ptr(key), _ptr(pred), _ptr(ts), n)
+    tr = _Trace(_ptr(key), _ptr(pred), _ptr(ts), n, _ptr(value))
     need = workspace_size(formula, n, not on_device, opts)
     if ws is None:
         ws = workspace(need)
@@ -267,11 +273,11 @@ def verify(formula: Formula, key, pred, ts=None, stream=None, want_bindings=Fals
     return res
 
 
-def verify_async(formula: Formula, key, pred, ws, dev_result, stream=None, opts=None, ts=None):
+def verify_async(formula: Formula, key, pred, ws, dev_result, stream=None, opts=None, ts=None, value=None):
     """Enqueue verification of a device-resident trace; the result lands in
     dev_result (a torch uint8 CUDA tensor of RESULT_BYTES bytes)."""
     n = int(pred.shape[0])
-    tr = _Trace(_ptr(key), _ptr(pred), _ptr(ts), n)
+    tr = _Trace(_ptr(key), _ptr(pred), _ptr(ts), n, _ptr(value))
     _check(lib().rv_verify_trace_async(formula.handle, ctypes.byref(tr), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
                                        ctypes.c_void_p(dev_result.data_ptr()), None, _opts(opts),
                                        _stream_handle(stream)))
@@ -283,7 +289,7 @@ def parse_result(raw: bytes) -> Result:
 
 
 # ---------------------------------------------------------------------- per-event timeline
-def timeline(formula: Formula, key, pred, stream=None):
+def timeline(formula: Formula, key, pred, stream=None, value=None):
     """Per-event verdicts and first violations of a device trace
     (rv_verify_timeline).  Returns (verdicts: np.uint8[n] in trace order,
     first_violation: {binding key: event index})."""
@@ -302,7 +308,7 @@ def timeline(formula: Formula, key, pred, stream=None):
     vidx = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
     nv = torch.zeros(1, dtype=torch.int64, device=dev)
     ws = workspace(int(L.rv_timeline_workspace_size(formula.handle, n)))
-    tr = _Trace(_ptr(key), _ptr(pred), None, n)
+    tr = _Trace(_ptr(key), _ptr(pred), None, n, _ptr(value))
     _check(L.rv_verify_timeline(formula.handle, ctypes.byref(tr), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
                                 _ptr(verd), _ptr(vkey), _ptr(vidx), _ptr(nv), _stream_handle(stream)))
     k = int(nv.item())
@@ -319,7 +325,8 @@ def _shard_sigs(L):
     L.rv_shard_of.argtypes = [vp, vp, u64, ctypes.c_int, vp]
     L.rv_shard_workspace_size.argtypes = [u64, ctypes.c_int]
     L.rv_shard_workspace_size.restype = ctypes.c_size_t
-    L.rv_shard_trace.argtypes = [vp, ctypes.POINTER(_Trace), ctypes.c_int, vp, ctypes.c_size_t, vp, vp, vp, vp, vp]
+    L.rv_shard_trace.argtypes = [vp, ctypes.POINTER(_Trace), ctypes.c_int, vp, ctypes.c_size_t, vp, vp, vp, vp, vp,
+                                 vp]
     L.rv_combine_results.argtypes = [vp, ctypes.POINTER(_Result), ctypes.c_int, ctypes.POINTER(_Result)]
     L._shard_sigs = True
 
@@ -334,10 +341,11 @@ def shard_of(formula: Formula, key, world: int) -> np.ndarray:
     return out
 
 
-def shard_trace(formula: Formula, key, pred, world: int, ts=None, stream=None):
+def shard_trace(formula: Formula, key, pred, world: int, ts=None, stream=None, value=None):
     """Group a device trace into world contiguous segments by rank (rv_shard_trace).
     Returns (key_out, pred_out, ts_out or None, counts) with counts a device
-    uint64 tensor (as int64) of the segment sizes."""
+    uint64 tensor (as int64) of the segment sizes; with value, the moved
+    values are in the attribute shard_trace.last_value."""
     import torch
     L = lib()
     _shard_sigs(L)
@@ -345,11 +353,14 @@ def shard_trace(formula: Formula, key, pred, world: int, ts=None, stream=None):
     key_out = torch.empty_like(key)
     pred_out = torch.empty_like(pred)
     ts_out = None if ts is None else torch.empty_like(ts)
+    value_out = None if value is None else torch.empty_like(value)
     counts = torch.empty(world, dtype=torch.int64, device=pred.device)
     ws = workspace(int(L.rv_shard_workspace_size(n, world)))
-    tr = _Trace(_ptr(key), _ptr(pred), _ptr(ts), n)
+    tr = _Trace(_ptr(key), _ptr(pred), _ptr(ts), n, _ptr(value))
     _check(L.rv_shard_trace(formula.handle, ctypes.byref(tr), world, ctypes.c_void_p(ws.data_ptr()), ws.numel(),
-                            _ptr(key_out), _ptr(pred_out), _ptr(ts_out), _ptr(counts), _stream_handle(stream)))
+                            _ptr(key_out), _ptr(pred_out), _ptr(ts_out), _ptr(value_out), _ptr(counts),
+                            _stream_handle(stream)))
+    shard_trace.last_value = value_out
     return key_out, pred_out, ts_out, counts
 
 

@@ -42,6 +42,7 @@ class Trace:
     key: np.ndarray
     codes: list
     meta: dict = field(default_factory=dict)
+    value: np.ndarray = None      # optional per-event value column (uint32)
 
     @property
     def n(self):
@@ -155,6 +156,34 @@ def file_trace(n_target, n_users, n_files, pairs_per_user=200, mean_events=10.0,
     meta = {"n_users": n_users, "n_pairs": n_pairs, "violating_users": users[violators & (want >= 4)],
             "leaked_pairs": int(leaked.sum())}
     return Trace(_timestamps(rng, n), pred[order], full_key[pair_of[order]], list(FILE_CODES), meta)
+
+
+CHUNK_CODES = ["user", "upload"]
+
+
+def chunk_trace(n, n_users, max_chunk=4 << 20, heavy_frac=0.05, seed=0):
+    """Case-study-2-shaped trace (personal cloud storage uploads): events of
+    uniformly chosen users, each carrying a chunk size; a user's first event
+    is ``user``, the others ``upload``.  The value column is the average chunk
+    size of the user's session so far (integer), the program variable the
+    case study's avg_chunksize predicate reads.  A share ``heavy_frac`` of the
+    users upload chunks of the maximum size only; the others draw sizes
+    log-uniformly in [4 KiB, max_chunk]."""
+    rng = np.random.default_rng(seed)
+    users = rng.choice(np.iinfo(np.uint32).max, size=n_users, replace=False).astype(np.uint32)
+    kidx = rng.integers(0, n_users, size=n, dtype=np.int64)
+    heavy = rng.random(n_users) < heavy_frac
+    size = np.exp(rng.uniform(np.log(4096), np.log(max_chunk), size=n)).astype(np.uint64)
+    size[heavy[kidx]] = max_chunk
+    rank, counts, order, starts = _rank_within_key(kidx, n_users)
+    csum = np.cumsum(size[order])
+    before = np.where(starts[:-1] > 0, csum[np.maximum(starts[:-1] - 1, 0)], 0).astype(np.uint64)
+    run = np.empty(n, dtype=np.uint64)
+    run[order] = csum - np.repeat(before, counts)
+    avg = (run // (rank.astype(np.uint64) + 1)).astype(np.uint32)
+    pred = np.where(rank == 0, 0, 1).astype(np.uint8)
+    meta = {"heavy_users": users[heavy & (counts > 0)], "appearing": int((counts > 0).sum()), "max_chunk": max_chunk}
+    return Trace(_timestamps(rng, n), pred, users[kidx], list(CHUNK_CODES), meta, avg)
 
 
 def batch_traces(n_traces, min_len=1_000, max_len=10_000_000, per_key=64, seed=0):
