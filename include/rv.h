@@ -234,6 +234,43 @@ rv_status rv_verify_timeline(const rv_formula* f, const rv_trace* t, void* ws, s
                              uint8_t* event_verdicts, uint64_t* viol_keys, uint32_t* viol_index,
                              uint64_t* n_viol, cudaStream_t s);
 
+/* ------------------------------------------------------------------ front end: strace text -> events
+ * The paper monitors programs through strace; its parsing module translates
+ * strace strings into a numerical table (Sec. 5).  rv_parse_strace does that
+ * on the GPU.  Each line of `text` (device memory, `bytes` long, lines ended
+ * by '\n', a last unterminated line included) has the form
+ *     [pid] TIME NAME(ARGS...) = RET [ERRNO (text)]
+ * with the pid optional ("[pid N] " or "N ") and TIME either
+ * seconds.microseconds (strace -ttt) or HH:MM:SS.microseconds (-tt).  A line
+ * whose NAME matches a rule becomes one event: pred = the rule's code, key =
+ * the first argument (RV_KEY_ARG0, e.g. the descriptor a read or close works
+ * on) or the return value (RV_KEY_RET, e.g. the descriptor socket or accept
+ * makes), ts = TIME in microseconds.  A call that strace -f splits into
+ * "NAME(ARGS <unfinished ...>" and "<... NAME resumed> ...) = RET" yields one
+ * event, from the line that holds its key.  Lines of other calls, signals and
+ * exits, calls whose key is missing, and failed calls (RET < 0) when the rule
+ * sets ok_only (RV_KEY_RET rules always need RET >= 0) are dropped.  Events
+ * keep the order of their lines.
+ * key_out (uint32), pred_out (uint8) and ts_out (uint64, may be NULL) are
+ * device arrays of `capacity` entries; *n_events (host) receives the number
+ * of events; more than capacity returns RV_ENOMEM after writing the first
+ * capacity.  ws: device workspace of rv_parse_workspace_size(bytes) bytes.
+ * Runs on s and returns when the table is complete.  1..16 rules, names of
+ * at most 23 characters.  Errors: RV_EINVAL, RV_ENOMEM, RV_ECUDA. */
+#define RV_PARSE_MAX_RULES 16
+#define RV_PARSE_NAME_LEN 24
+enum { RV_KEY_ARG0 = 0, RV_KEY_RET = 1 };
+typedef struct {
+  const char* name;   /* system call name, e.g. "recvfrom" */
+  int code;           /* predicate code of its events */
+  int key_from;       /* RV_KEY_ARG0 or RV_KEY_RET */
+  int ok_only;        /* nonzero: drop calls that returned a negative value */
+} rv_syscall_rule;
+size_t rv_parse_workspace_size(uint64_t bytes);
+rv_status rv_parse_strace(const char* text, uint64_t bytes, const rv_syscall_rule* rules, int n_rules,
+                          void* ws, size_t ws_bytes, uint32_t* key_out, uint8_t* pred_out, uint64_t* ts_out,
+                          uint64_t capacity, uint64_t* n_events, cudaStream_t s);
+
 /* ------------------------------------------------------------------ one trace over several ranks
  * Algorithm 1 (Sec. 4.2) evaluates every binding on its own projection
  * (Sec. 2.4.3); all bindings of one outer value d_0 form one subtree of the

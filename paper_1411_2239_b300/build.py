@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "librv.so")
-SOURCES = ["formula.cpp", "profile.cpp", "offline.cu", "batch.cu", "stream.cu", "shard.cu", "timeline.cu", "noalloc.cu"]
+SOURCES = ["formula.cpp", "profile.cpp", "offline.cu", "batch.cu", "stream.cu", "shard.cu", "timeline.cu", "parse.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -288,6 +288,51 @@ def parse_result(raw: bytes) -> Result:
     return _result(r)
 
 
+# ---------------------------------------------------------------------- front end: strace text
+KEY_ARG0, KEY_RET = 0, 1
+
+
+class _Rule(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char_p), ("code", ctypes.c_int), ("key_from", ctypes.c_int),
+                ("ok_only", ctypes.c_int)]
+
+
+def parse_strace(text, rules, capacity=None, stream=None):
+    """Event table of a strace log (rv_parse_strace).  text: bytes/str (copied
+    to the device) or a torch uint8 CUDA tensor; rules: (name, code, key_from,
+    ok_only) tuples.  Returns device tensors (key int32 view of uint32, pred
+    uint8, ts int64 microseconds) of the events."""
+    import torch
+    L = lib()
+    if not getattr(L, "_parse_sigs", False):
+        vp = ctypes.c_void_p
+        L.rv_parse_workspace_size.argtypes = [ctypes.c_uint64]
+        L.rv_parse_workspace_size.restype = ctypes.c_size_t
+        L.rv_parse_strace.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(_Rule), ctypes.c_int, vp, ctypes.c_size_t,
+                                      vp, vp, vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64), vp]
+        L._parse_sigs = True
+    if isinstance(text, str):
+        text = text.encode()
+    if not isinstance(text, torch.Tensor):
+        text = torch.frombuffer(bytearray(text), dtype=torch.uint8).cuda() if len(text) else \
+            torch.empty(0, dtype=torch.uint8, device="cuda")
+    nbytes = int(text.numel())
+    cap = capacity if capacity is not None else max(1, nbytes // 16 + 1)
+    names = [r[0].encode() for r in rules]
+    arr = (_Rule * len(rules))(*[_Rule(nm, int(r[1]), int(r[2]), int(r[3]) if len(r) > 3 else 0)
+                                 for nm, r in zip(names, rules)])
+    key = torch.empty(cap, dtype=torch.int32, device=text.device)
+    pred = torch.empty(cap, dtype=torch.uint8, device=text.device)
+    ts = torch.empty(cap, dtype=torch.int64, device=text.device)
+    ws = workspace(int(L.rv_parse_workspace_size(nbytes)))
+    n = ctypes.c_uint64()
+    _check(L.rv_parse_strace(_ptr(text) if nbytes else None, nbytes, arr, len(rules), ctypes.c_void_p(ws.data_ptr()),
+                             ws.numel(), _ptr(key), _ptr(pred), _ptr(ts), cap, ctypes.byref(n),
+                             _stream_handle(stream)))
+    k = n.value
+    return key[:k], pred[:k], ts[:k]
+
+
 # ---------------------------------------------------------------------- per-event timeline
 def timeline(formula: Formula, key, pred, stream=None, value=None):
     """Per-event verdicts and first violations of a device trace

@@ -234,3 +234,57 @@ def random_quantifier(rng):
     if rng.random() < 0.5:
         return f"A_{{{op}{int(rng.integers(0, 21)) * 5}%}}"
     return f"E_{{{op}{int(rng.integers(0, 9))}}}"
+
+
+def strace_log(trace, seed=0, noise=0.3, split=0.1, fmt="ttt"):
+    """strace text of a socket trace (codes socket / receive / respond): each
+    event becomes a socket(...) = id, recvfrom(id, ...) or sendto(id, ...) line;
+    between them come lines the front end must drop (other calls, failed
+    receives, signals, exits) and, for a share ``split`` of the events, the
+    call is cut into an unfinished and a resumed half with another line in
+    between.  Timestamps: strace -ttt or -tt format, microseconds."""
+    rng = np.random.default_rng(seed)
+    pids = rng.integers(1000, 99999, size=4)
+    t0 = 1_700_000_000 * 1_000_000
+    out = []
+
+    def stamp(t):
+        sec, us = divmod(int(t), 1_000_000)
+        if fmt == "ttt":
+            return f"{sec}.{us:06d}"
+        h, rem = divmod(sec % 86400, 3600)
+        return f"{h:02d}:{rem // 60:02d}:{rem % 60:02d}.{us:06d}"
+
+    def pid():
+        p = int(pids[int(rng.integers(len(pids)))])
+        return f"[pid {p:5d}] " if rng.random() < 0.5 else f"{p} "
+
+    noise_lines = ["epoll_wait(4, [], 512, 0) = 0", "futex(0x7f3a2c0, FUTEX_WAKE_PRIVATE, 1) = 1",
+                   "mmap(NULL, 8192, PROT_READ|PROT_WRITE, MAP_PRIVATE|MAP_ANONYMOUS, -1, 0) = 0x7f3a2c000000",
+                   "recvfrom(9, 0x7ffd, 8192, 0, NULL, NULL) = -1 EAGAIN (Resource temporarily unavailable)",
+                   "--- SIGCHLD {si_signo=SIGCHLD, si_code=CLD_EXITED, si_pid=4242} ---",
+                   "+++ exited with 0 +++", "close(11) = 0", "accept4(3, NULL, NULL, SOCK_CLOEXEC) = -1 EAGAIN (x)"]
+    t = t0
+    for key, code in zip(trace.key.tolist(), trace.pred.tolist()):
+        t += int(rng.integers(1, 50))
+        while rng.random() < noise:
+            out.append(f"{pid()}{stamp(t)} {noise_lines[int(rng.integers(len(noise_lines)))]}")
+        n = int(rng.integers(1, 4000))
+        if code == 0:
+            head, tail = "socket(AF_INET, SOCK_STREAM, IPPROTO_TCP", f") = {key}"
+            name = "socket"
+        elif code == 1:
+            head, tail = f'recvfrom({key}, "GET /index.html HTTP/1.1\r\n"..., 8192, 0, NULL', f", NULL) = {n}"
+            name = "recvfrom"
+        else:
+            head, tail = f'sendto({key}, "HTTP/1.1 200 OK\r\n"..., {n}, MSG_NOSIGNAL, NULL', f", 0) = {n}"
+            name = "sendto"
+        if rng.random() < split:
+            p = pid()
+            out.append(f"{p}{stamp(t)} {head} <unfinished ...>")
+            out.append(f"{pid()}{stamp(t)} {noise_lines[0]}")
+            out.append(f"{p}{stamp(t + 1)} <... {name} resumed>{tail}")
+        else:
+            out.append(f"{pid()}{stamp(t)} {head}{tail}")
+    return "\n".join(out) + "\n"
+
