@@ -243,6 +243,8 @@ def strace_log(trace, seed=0, noise=0.3, split=0.1, fmt="ttt"):
     receives, signals, exits) and, for a share ``split`` of the events, the
     call is cut into an unfinished and a resumed half with another line in
     between.  Timestamps: strace -ttt or -tt format, microseconds."""
+    if not 0.0 <= noise < 1.0:
+        raise ValueError("noise is the probability of one more dropped line: it must lie in [0, 1)")
     rng = np.random.default_rng(seed)
     pids = rng.integers(1000, 99999, size=4)
     t0 = 1_700_000_000 * 1_000_000
