@@ -1,14 +1,16 @@
 """Throughput benchmark: verified events/s of map -> monitor -> reduce on B300.
 
-    python bench.py [--gpus N --steps K --warmup W] [--workload c2|c1|c3|c4|c5] [--only]
+    python bench.py [--gpus N --steps K --warmup W] [--workload c2|c1|c3|c4|c5|timeline|shard8|strace] [--only]
     python bench.py --impl reference ...      # the CPU oracle on the same workload
 
 A step is one rv_verify_trace of the whole synthetic trace (all stages: key
 multisplit, monitor fold, combine, quantifier reduce) with the trace already
 resident in HBM.  The default line is the 1e8-event Zipf socket trace; its
-``workloads`` object adds, measured in the same run, the nested two-variable
-trace, the batched 256 x 32 run (against one launch per trace and formula)
-and the serving run (p50/p99 latency); ``--only`` leaves them out.  Traces
+``workloads`` object adds, measured in the same run, the per-event timeline
+and the 8-way split of that trace, the strace front end (text -> events ->
+verdict), the nested two-variable trace, the batched 256 x 32 run (against
+one launch per trace and formula) and the serving run (p50/p99 latency);
+``--only`` leaves them out.  Traces
 are larger than L2, so no flush is needed between steps.  ``e2e`` repeats the
 measurement through the same C ABI with pinned HOST buffers: the host->device
 copy of the events and the device->host copy of the verdict are inside its
@@ -472,7 +474,76 @@ def bench_offline(args, wname, full=True):
                       "host_link_gbs": (hk.nbytes + hp.nbytes) / max(dt - ms / 1e3, 1e-9) / 1e9}
     if full and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(w, trace)
+    bench_offline.last = (trace, f, key, pred)
     return out
+
+
+def _time(fn, steps, warmup):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        r = fn()
+    torch.cuda.synchronize()
+    return (time.perf_counter() - t0) / steps, r
+
+
+def bench_timeline(args, trace, f, key, pred):
+    """Per-event verdicts and first violations of the whole trace (rv_verify_timeline)."""
+    from paper_1411_2239_b300 import rv
+    steps = max(1, min(args.steps, 5))
+    dt, (v, first) = _time(lambda: rv.timeline(f, key, pred), steps, 1)
+    pk, _ = peaks()
+    n = trace.n
+    return {"value": n / dt, "unit": "events/s", "ms_per_step": dt * 1e3, "steps": steps,
+            "verdict_histogram": np.bincount(v, minlength=6).tolist(), "violated_bindings": len(first),
+            "note": "host-timed, includes the read-back of the per-event verdicts and violations",
+            "path_frac_of_hbm": (ALG_BYTES["c2"] + 1) * n / dt / 1e9 / pk["hbm_gbs"]}
+
+
+def bench_shard(args, trace, f, key, pred, world=8):
+    """The device split of one trace into `world` parts by outer-value hash (rv_shard_trace)."""
+    import torch
+    from paper_1411_2239_b300 import rv
+    ks, ps, _, counts = rv.shard_trace(f, key, pred, world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    steps = max(1, args.steps)
+    for _ in range(steps):
+        rv.shard_trace(f, key, pred, world)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    pk, _ = peaks()
+    n = trace.n
+    moved = 2 * ALG_BYTES["c2"] * n                     # read and write of key and predicate
+    c = counts.cpu().tolist()
+    return {"value": n / (ms / 1e3), "unit": "events/s", "ms_per_step": ms, "steps": steps, "world": world,
+            "part_sizes": c, "hbm_frac": moved / (ms / 1e3) / 1e9 / pk["hbm_gbs"]}
+
+
+def bench_strace(args, n_events=1_000_000):
+    """strace text of a socket trace parsed on the GPU (rv_parse_strace), then verified."""
+    import torch
+    from paper_1411_2239_b300 import rv, synth
+    tr = synth.socket_trace(n_events, 10_000, pending_frac=0.03, zipf_s=1.1, seed=6000)
+    text = synth.strace_log(tr, seed=6001)
+    dev = torch.frombuffer(bytearray(text.encode()), dtype=torch.uint8).cuda()
+    rules = [("socket", 0, rv.KEY_RET, 0), ("recvfrom", 1, rv.KEY_ARG0, 1), ("sendto", 2, rv.KEY_ARG0, 1)]
+    steps = max(1, min(args.steps, 10))
+    dt, (key, pred, ts) = _time(lambda: rv.parse_strace(dev, rules, capacity=n_events + 16), steps, 2)
+    ok = key.numel() == tr.n and (key.cpu().numpy().view(np.uint32) == tr.key).all()
+    f = rv.Formula(WORKLOADS["c2"]["formula"], tr.codes)
+    r = rv.verify(f, key, pred)
+    ok = bool(ok and r.root_counts == expected_counts(dict(WORKLOADS["c2"], kind="socket"), tr)["root_counts"])
+    pk, _ = peaks()
+    return {"value": tr.n / dt, "unit": "events/s", "text_bytes": int(dev.numel()), "text_gbs": dev.numel() / dt / 1e9,
+            "ms_per_step": dt * 1e3, "steps": steps, "verified": ok,
+            "hbm_frac": dev.numel() / dt / 1e9 / pk["hbm_gbs"],
+            "note": "host-timed, includes the read-back of the event count"}
 
 
 # ---------------------------------------------------------------------- batched (config 4)
@@ -671,13 +742,15 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=list(WORKLOADS))
+    ap.add_argument("--workload", default="c2", choices=list(WORKLOADS) + ["timeline", "shard8", "strace"])
     ap.add_argument("--only", action="store_true", help="the headline workload alone (no workloads object)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--events", type=int, default=0,
                     help="shrink the workload to about this many events (ids scale with it); profiling only")
     args = ap.parse_args()
+    if args.workload in ("timeline", "shard8", "strace"):   # one of the c2 trace's sub-runs alone
+        return run_sub(args)
     if args.events:
         w = WORKLOADS[args.workload]
         scale = args.events / w["n"]
@@ -715,7 +788,11 @@ def main():
             line[k] = sub[k]
     if not args.only and args.workload == "c2" and not args.events:
         line["workloads"] = {}
-        for name, fn in (("c3", lambda: bench_offline(args, "c3", full=False)), ("c4", lambda: bench_batch(args)),
+        tr, f, key, pred = bench_offline.last
+        for name, fn in (("timeline", lambda: bench_timeline(args, tr, f, key, pred)),
+                         ("shard8", lambda: bench_shard(args, tr, f, key, pred)),
+                         ("strace", lambda: bench_strace(args)),
+                         ("c3", lambda: bench_offline(args, "c3", full=False)), ("c4", lambda: bench_batch(args)),
                          ("c5", lambda: bench_serve(args))):
             t0 = time.perf_counter()
             try:
@@ -724,6 +801,29 @@ def main():
                 line["workloads"][name] = {"error": f"{type(e).__name__}: {e}"}
             line["workloads"][name]["wall_s"] = time.perf_counter() - t0
     print(json.dumps(line))
+
+
+def run_sub(args):
+    """One of the sub-runs of the default line on its own (profiling): the
+    c2 trace (shrunk with --events) for the timeline and the split, a
+    generated strace log for the front end."""
+    import torch
+    from paper_1411_2239_b300 import rv
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    if args.workload == "strace":
+        out = bench_strace(args, n_events=args.events or 1_000_000)
+    else:
+        w = WORKLOADS["c2"]
+        if args.events:
+            scale = args.events / w["n"]
+            w["n"], w["n_ids"] = args.events, max(10, int(w["n_ids"] * scale))
+        tr = make_trace(w, 1000 * w["cfg"])
+        f = rv.Formula(w["formula"], tr.codes)
+        key = torch.from_numpy(tr.key.view(np.int32)).cuda()
+        pred = torch.from_numpy(tr.pred).cuda()
+        fn = bench_timeline if args.workload == "timeline" else bench_shard
+        out = fn(args, tr, f, key, pred)
+    print(json.dumps({"workload": args.workload, **out}))
 
 
 class StatArr(ctypes.Structure):

@@ -1,6 +1,7 @@
 """Build librv.so (host compiler + sm_103a kernels) in-tree with nvcc.
 
     python -m paper_1411_2239_b300.build        # rebuild if any source changed
+    RV_CHECKED=1 python -m paper_1411_2239_b300.build --force   # bounds-checked test build
 """
 from __future__ import annotations
 
@@ -47,6 +48,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
         obj = os.path.join(tmpdir, os.path.basename(src) + ".o")
         cmd = [_nvcc(), "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC",
                "-I", os.path.join(ROOT, "include"), "-c", src, "-o", obj]
+        if os.environ.get("RV_CHECKED"):       # bounds-checked test build (see offline.cu)
+            cmd.insert(1, "-DRV_CHECKED")
         if src.endswith(".cpp"):
             cmd[1:1] = ["-x", "cu"]
         if verbose:

@@ -61,6 +61,21 @@ constexpr int BATCH = 16;      // rounds of 32 events whose loads are issued tog
 constexpr int HVEC = 4;        // 16-byte loads in flight per lane in the level-2 histogram
 
 struct Tile { uint32_t bucket, k, K, pad; uint64_t begin, end; };
+
+// Bounds-checked builds (-DRV_CHECKED, for test runs): the global writes of
+// the multisplit, tile and unit lists, fold and combine check their index
+// against the array's size; a write outside is skipped and reported through
+// the status word (ERR_BOUNDS, status RV_EINTERNAL) instead of faulting.
+// The sizes of one verification are set before its kernels, so checked
+// builds are for one verification at a time.
+#ifdef RV_CHECKED
+struct CheckCaps { unsigned long long n, tiles2, units, pool; };
+__device__ CheckCaps g_caps;
+__device__ unsigned int g_bounds_err;
+#define RV_INB(i, cap) ((unsigned long long)(i) < (cap) ? true : (atomicOr(&g_bounds_err, 1u), false))
+#else
+#define RV_INB(i, cap) true
+#endif
 struct Item { uint64_t off; uint32_t cnt, pad; };
 struct Group { uint32_t bucket, first, cnt, k, K, pad; };
 struct Pair { uint64_t key, map; };
@@ -269,7 +284,8 @@ k_scatter_tile(const void* keyp, const uint8_t* pred, uint64_t n, int nq, int n_
   // 5. runs of each bucket go out contiguously, gathered through perm
   for (int j = threadIdx.x; j < len; j += TB_THREADS) {
     const uint32_t i = S.perm[j], b = S.sb[i];
-    out[S.gbase[b] + (j - S.loc[b])] = S.srec[i];
+    const uint64_t o = S.gbase[b] + (j - S.loc[b]);
+    if (RV_INB(o, g_caps.n)) out[o] = S.srec[i];
   }
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&acc->err, ERR_LETTER);
 }
@@ -410,7 +426,7 @@ k_scatter(const void* keyp, const uint8_t* pred, uint64_t n, uint64_t per_warp, 
       __syncwarp();
       if (v && lane == __ffs(peers) - 1) cur[b[j]] += __popc(peers);
       __syncwarp();
-      if (v) out[pos] = rec[j];
+      if (v && RV_INB(pos, g_caps.n)) out[pos] = rec[j];
     }
   }
   if (__any_sync(FULL, bad) && lane == 0) atomicOr(&acc->err, ERR_LETTER);
@@ -526,7 +542,7 @@ __global__ void k_count_units(const uint64_t* bstart, int P, int B2, uint64_t un
 // one thread per tile: binary search of its bucket in first[]; with uend, a
 // bucket of at most half a tile heads a shared tile that ends at uend[b]
 __global__ void k_emit_tiles(const uint64_t* bstart, int P, uint64_t tile_len, const uint32_t* first, const uint32_t* K,
-                             const unsigned int* n_tiles, Tile* tiles, const uint64_t* uend = nullptr) {
+                             const unsigned int* n_tiles, Tile* tiles, uint64_t cap, const uint64_t* uend = nullptr) {
   const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= *n_tiles) return;
   int lo = 0, hi = P - 1;            // last bucket with first[b] <= t and K[b] > 0
@@ -541,7 +557,7 @@ __global__ void k_emit_tiles(const uint64_t* bstart, int P, uint64_t tile_len, c
   tl.begin = bstart[lo] + j * tile_len;
   tl.end = min(bstart[lo + 1], tl.begin + tile_len);
   if (uend && bstart[lo + 1] - bstart[lo] <= tile_len / 2) tl.end = uend[lo];
-  tiles[t] = tl;
+  if (RV_INB(t, cap)) tiles[t] = tl;
 }
 
 // ------------------------------------------------------------------ heavy bindings
@@ -727,7 +743,8 @@ k_hist2(const typename RecT<F>::type* recs, const Tile* tiles, const unsigned in
     }
   }
   __syncwarp();
-  for (int b = lane; b < P2; b += 32) hist2[(uint64_t)tile * P2 + b] = cnt[b];
+  if (RV_INB(tile, g_caps.tiles2))
+    for (int b = lane; b < P2; b += 32) hist2[(uint64_t)tile * P2 + b] = cnt[b];
 }
 
 // per (first-level bucket, sub-bucket): exclusive prefix over the bucket's
@@ -864,7 +881,7 @@ k_scatter2(const typename RecT<F>::type* in, const Tile* tiles, const unsigned i
       __syncwarp();
       if (v && lane == __ffs(peers) - 1) cur[b[j]] += __popc(peers);
       __syncwarp();
-      if (v) out[pos] = rec[j];
+      if (v && RV_INB(pos, g_caps.n)) out[pos] = rec[j];
     }
   }
 }
@@ -943,7 +960,8 @@ k_scatter2_tile(const typename RecT<F>::type* in, const Tile* tiles, const unsig
   __syncthreads();
   for (int i = threadIdx.x; i < len; i += TB_THREADS) {
     const uint32_t b = S.ob[i];
-    out[S.gbase[b] + (i - S.loc[b])] = S.orec[i];
+    const uint64_t o = S.gbase[b] + (i - S.loc[b]);
+    if (RV_INB(o, g_caps.n)) out[o] = S.orec[i];
   }
 }
 
@@ -1540,7 +1558,7 @@ k_fold(const typename RecT<F>::type* recs, const Tile* units, const unsigned int
           uint64_t T = S.wmaps[0];
           for (int w = 1; w < FOLD_WARPS; ++w) T = apply_map(T, S.wmaps[w], ns);
           if (single) fold_finalize<F>(p, fc, S, 0, (uint64_t)cand, T, t.bucket);
-          else pool[S.item_off] = Pair{(uint64_t)cand, T};
+          else if (RV_INB(S.item_off, g_caps.pool)) pool[S.item_off] = Pair{(uint64_t)cand, T};
           S.item_cnt = 1;
           S.npass = 0;
         }
@@ -1687,7 +1705,7 @@ k_fold(const typename RecT<F>::type* recs, const Tile* units, const unsigned int
             }
             if (starts && ends) {
               if (single) fold_finalize<F>(p, fc, S, sl, S.skey[sl], V, t.bucket);
-              else pool[S.item_off + S.item_cnt + sl] = Pair{S.skey[sl], V};
+              else if (RV_INB(S.item_off + S.item_cnt + sl, g_caps.pool)) pool[S.item_off + S.item_cnt + sl] = Pair{S.skey[sl], V};
             } else if (!starts) {
               S.firstmap[threadIdx.x] = V;          // continues a run begun in an earlier piece
             } else {
@@ -1733,7 +1751,7 @@ k_fold(const typename RecT<F>::type* recs, const Tile* units, const unsigned int
             }
           }
           if (single) fold_finalize<F>(p, fc, S, sl, S.skey[sl], V, t.bucket);
-          else pool[S.item_off + S.item_cnt + sl] = Pair{S.skey[sl], V};
+          else if (RV_INB(S.item_off + S.item_cnt + sl, g_caps.pool)) pool[S.item_off + S.item_cnt + sl] = Pair{S.skey[sl], V};
         }
       }
       // the dominant candidate: each thread folds its contiguous piece of the
@@ -1756,7 +1774,7 @@ k_fold(const typename RecT<F>::type* recs, const Tile* units, const unsigned int
           uint64_t T = S.wmaps[0];
           for (int w = 1; w < FOLD_WARPS; ++w) T = apply_map(T, S.wmaps[w], ns);
           if (single) fold_finalize<F>(p, fc, S, 0, S.skey[0], T, t.bucket);
-          else pool[S.item_off + S.item_cnt + 0] = Pair{S.skey[0], T};
+          else if (RV_INB(S.item_off + S.item_cnt, g_caps.pool)) pool[S.item_off + S.item_cnt + 0] = Pair{S.skey[0], T};
         }
       }
       if constexpr (F == FMT_K2) {
@@ -1984,7 +2002,7 @@ k_combine(const Item* items_in, const Pair* pool_in, const Group* groups, const 
       const unsigned int nsl = min(S.T.nslots, (unsigned int)SLOTS);
       for (unsigned int s = threadIdx.x; s < nsl; s += blockDim.x) {
         if (final_) finalize_slot<F>(p, fc, &S.U, S.T.skey[s], S.smap[s], G.bucket);
-        else pool_out[S.out_off + S.out_cnt + s] = Pair{S.T.skey[s], S.smap[s]};
+        else if (RV_INB(S.out_off + S.out_cnt + s, g_caps.pool)) pool_out[S.out_off + S.out_cnt + s] = Pair{S.T.skey[s], S.smap[s]};
       }
       __syncthreads();
       if (threadIdx.x == 0) { S.out_cnt += nsl; S.npass -= 1; }
@@ -1996,6 +2014,13 @@ k_combine(const Item* items_in, const Pair* pool_in, const Group* groups, const 
   __syncthreads();
   flush_final(p, fc);
 }
+
+#ifdef RV_CHECKED
+// the bounds-check word of this verification, into its status word
+__global__ void k_bounds(Acc* acc) {
+  if (g_bounds_err) { atomicOr(&acc->err, (unsigned)ERR_BOUNDS); g_bounds_err = 0; }
+}
+#endif
 
 __global__ void k_root(Acc* acc, Params p, uint64_t n, rv_result* out, int test_wait_polls) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -2180,6 +2205,15 @@ static rv_status launch_all(const Plan& pl, const rv_formula* f, const void* key
   typedef typename RecT<F>::type Rec;
   Acc* acc = (Acc*)(ws + pl.o_acc);
   RV_CU(cudaMemsetAsync(acc, 0, sizeof(Acc), s));
+#ifdef RV_CHECKED
+  {
+    const CheckCaps caps{pl.n, pl.max_tiles2, pl.max_units, std::max<uint64_t>(pl.n, 1)};
+    const unsigned int zero = 0;
+    RV_CU(cudaMemcpyToSymbolAsync(g_caps, &caps, sizeof caps, 0, cudaMemcpyHostToDevice, s));
+    RV_CU(cudaMemcpyToSymbolAsync(g_bounds_err, &zero, 4, 0, cudaMemcpyHostToDevice, s));
+    RV_CU(cudaStreamSynchronize(s));   // the sources are on this stack frame
+  }
+#endif
   if (f->n_cmp && pl.n) {              // comparison atoms: fold each event's value into its letter
     uint8_t* letters = ws + pl.o_letters;
     const unsigned g = (unsigned)std::min<uint64_t>((pl.n + 255) / 256, (uint64_t)num_sms() * 8);
@@ -2233,7 +2267,7 @@ static rv_status launch_all(const Plan& pl, const rv_formula* f, const void* key
       Rec* recB = (Rec*)(ws + pl.o_recB);
       RV_LAUNCH("k_count_tiles", k_count_tiles, (pl.P1 + 255) / 256, 256, 0, s, bstart1, pl.P1, pl.tile2, tk2);
       RV_LAUNCH("k_scan_u32", k_scan<uint32_t>, 1, 1024, scan_smem<uint32_t>(), s, tk2, pl.P1, tf2, &acc->n_tiles2);
-      RV_LAUNCH("k_emit_tiles", k_emit_tiles, (int)((pl.max_tiles2 + 255) / 256), 256, 0, s, bstart1, pl.P1, pl.tile2, tf2, tk2, &acc->n_tiles2, tiles2);
+      RV_LAUNCH("k_emit_tiles", k_emit_tiles, (int)((pl.max_tiles2 + 255) / 256), 256, 0, s, bstart1, pl.P1, pl.tile2, tf2, tk2, &acc->n_tiles2, tiles2, pl.max_tiles2);
       const int t2_blocks = (int)((pl.max_tiles2 + SC_WARPS - 1) / SC_WARPS);
       HeavyDev hv{nullptr, nullptr, 0};
       if (pl.heavy) {
@@ -2276,7 +2310,7 @@ static rv_status launch_all(const Plan& pl, const rv_formula* f, const void* key
     RV_LAUNCH("k_count_units", k_count_units, (pl.P + 255) / 256, 256, 0, s, bstart, pl.P, pl.B2e, pl.unit, F != FMT_K2 ? 1 : 0, uk, uend,
               pl.heavy ? 1 << pl.B2 : 0);
     RV_LAUNCH("k_scan_u32", k_scan<uint32_t>, 1, 1024, scan_smem<uint32_t>(), s, uk, pl.P, uf, &acc->n_units);
-    RV_LAUNCH("k_emit_tiles", k_emit_tiles, (int)((pl.max_units + 255) / 256), 256, 0, s, bstart, pl.P, pl.unit, uf, uk, &acc->n_units, units,
+    RV_LAUNCH("k_emit_tiles", k_emit_tiles, (int)((pl.max_units + 255) / 256), 256, 0, s, bstart, pl.P, pl.unit, uf, uk, &acc->n_units, units, pl.max_units,
               F != FMT_K2 ? uend : nullptr);
     const int grid = (int)std::min<uint64_t>(pl.max_units, (uint64_t)num_sms() * FoldCfg<F>::MINB);
     RV_LAUNCH("k_fold", k_fold<F>, grid, FOLD_THREADS, sizeof(FoldShared<F>), s, recs, units, &acc->n_units, p, items0, pool0);
@@ -2306,6 +2340,9 @@ static rv_status launch_all(const Plan& pl, const rv_formula* f, const void* key
       std::swap(pin, pout);
     }
   }
+#ifdef RV_CHECKED
+  RV_LAUNCH("k_bounds", k_bounds, 1, 1, 0, s, acc);
+#endif
   if (!ss) RV_LAUNCH("k_root", k_root, 1, 32, 0, s, acc, p, n, dev_out, pl.test_wait);
   RV_CU(cudaGetLastError());
   return RV_OK;

@@ -218,7 +218,8 @@ enum {
   ERR_TS = 2,           // timestamps decrease
   ERR_OUTER_FULL = 4,   // too many outer bindings in one bucket
   ERR_SPIN = 8,         // a bounded wait gave up
-  ERR_POOL = 16         // pair pool exhausted
+  ERR_POOL = 16,        // pair pool exhausted
+  ERR_BOUNDS = 128      // bounds-checked builds: a write fell outside its array (skipped)
 };
 
 struct Acc {
