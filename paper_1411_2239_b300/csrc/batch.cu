@@ -222,7 +222,7 @@ k_bscatter(BatchDev d, const uint32_t* key, const uint8_t* pred, const uint32_t*
 #pragma unroll
     for (int j = 0; j < BATCHR; ++j) {
       const bool v = b[j] != EMPTY32;
-      const uint32_t peers = match_bits<MAXBITS>(b[j], v);
+      const uint32_t peers = __match_any_sync(FULL, v ? b[j] : EMPTY32);   // lanes of equal buckets
       uint32_t pos = 0;
       if (v) pos = cur[b[j]] + __popc(peers & lt);
       __syncwarp();
@@ -380,7 +380,7 @@ __device__ bool fold_records(BFoldShared& S, const uint64_t* recs, uint64_t r0, 
       const int i = base + lane;
       const uint32_t sl = i < w1 ? S.slot_of[i] : (uint32_t)NO_SLOT;
       const bool v = sl != NO_SLOT;
-      const uint32_t peers = match_bits<10>(v ? sl : 0u, v);
+      const uint32_t peers = __match_any_sync(FULL, v ? sl : 0xFFFFFFFFu);   // lanes of equal slots
       uint32_t pos = 0;
       if (v) pos = S.wcnt[wl][sl] + __popc(peers & lt);
       __syncwarp();

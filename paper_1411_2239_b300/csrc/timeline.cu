@@ -52,17 +52,19 @@ k_t_hist(const K* key, uint64_t n, uint64_t per_warp, int G_w, int shift, uint32
   const uint64_t begin = (uint64_t)gw * per_warp, end = min(n, begin + per_warp);
   for (uint64_t i = begin + lane; i < end; i += 32) atomicAdd(&cnt[wl][(uint32_t)(key[i] >> shift) & 255u], 1u);
   __syncwarp();
-  for (int r = lane; r < 256; r += 32) hist[(uint64_t)gw * 256 + r] = cnt[wl][r];
+  for (int r = lane; r < 256; r += 32) hist[(uint64_t)r * G_w + gw] = cnt[wl][r];   // digit-major
 }
 
-// one CTA per digit value: exclusive prefix of its column over the warp slices
+// one CTA per digit value: exclusive prefix of its row over the warp slices
+// (rows are contiguous, the histogram being stored digit-major)
 __global__ void __launch_bounds__(1024) k_t_colscan(uint32_t* hist, int G_w, uint64_t* tot) {
   __shared__ uint64_t wsum[32];
   const int r = blockIdx.x;
+  uint32_t* row = hist + (uint64_t)r * G_w;
   const int per = (G_w + blockDim.x - 1) / blockDim.x;
   const int j0 = threadIdx.x * per, j1 = min(G_w, j0 + per);
   uint64_t mine = 0;
-  for (int j = j0; j < j1; ++j) mine += hist[(uint64_t)j * 256 + r];
+  for (int j = j0; j < j1; ++j) mine += row[j];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   uint64_t incl = mine;
   for (int d = 1; d < 32; d <<= 1) {
@@ -82,8 +84,8 @@ __global__ void __launch_bounds__(1024) k_t_colscan(uint32_t* hist, int G_w, uin
   __syncthreads();
   uint64_t run = (w ? wsum[w - 1] : 0) + incl - mine;
   for (int j = j0; j < j1; ++j) {
-    const uint32_t c = hist[(uint64_t)j * 256 + r];
-    hist[(uint64_t)j * 256 + r] = (uint32_t)run;
+    const uint32_t c = row[j];
+    row[j] = (uint32_t)run;
     run += c;
   }
   if (threadIdx.x == blockDim.x - 1) tot[r] = run;
@@ -104,7 +106,7 @@ k_t_scatter(const K* key, const uint32_t* idx, uint64_t n, uint64_t per_warp, in
   const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int gw = blockIdx.x * TW + wl;
   if (gw >= G_w) return;
-  for (int r = lane; r < 256; r += 32) cur[wl][r] = seg[r] + pre[(uint64_t)gw * 256 + r];
+  for (int r = lane; r < 256; r += 32) cur[wl][r] = seg[r] + pre[(uint64_t)r * G_w + gw];
   __syncwarp();
   const uint64_t begin = (uint64_t)gw * per_warp, end = min(n, begin + per_warp);
   const uint32_t lt = (1u << lane) - 1u;

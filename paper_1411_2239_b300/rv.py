@@ -338,6 +338,16 @@ def timeline(formula: Formula, key, pred, stream=None, value=None):
     """Per-event verdicts and first violations of a device trace
     (rv_verify_timeline).  Returns (verdicts: np.uint8[n] in trace order,
     first_violation: {binding key: event index})."""
+    verd, vkey, vidx, k = timeline_device(formula, key, pred, stream, value)
+    keys = vkey[:k].cpu().numpy().view(np.uint64).tolist()
+    idx = vidx[:k].cpu().numpy().view(np.uint32).tolist()
+    return verd.cpu().numpy(), dict(zip(keys, idx))
+
+
+def timeline_device(formula: Formula, key, pred, stream=None, value=None, out=None):
+    """rv_verify_timeline into device tensors: (verdicts uint8[n], violation
+    keys, violation indices, number of violations).  `out` reuses the output
+    tensors of an earlier call of the same size."""
     import torch
     L = lib()
     if not getattr(L, "_tl_sigs", False):
@@ -348,18 +358,16 @@ def timeline(formula: Formula, key, pred, stream=None, value=None):
         L._tl_sigs = True
     n = int(pred.shape[0])
     dev = pred.device
-    verd = torch.empty(max(n, 1), dtype=torch.uint8, device=dev)
-    vkey = torch.empty(max(n, 1), dtype=torch.int64, device=dev)
-    vidx = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
-    nv = torch.zeros(1, dtype=torch.int64, device=dev)
+    if out is None:
+        out = (torch.empty(max(n, 1), dtype=torch.uint8, device=dev), torch.empty(max(n, 1), dtype=torch.int64, device=dev),
+               torch.empty(max(n, 1), dtype=torch.int32, device=dev), torch.zeros(1, dtype=torch.int64, device=dev))
+    verd, vkey, vidx, nv = out
     ws = workspace(int(L.rv_timeline_workspace_size(formula.handle, n)))
     tr = _Trace(_ptr(key), _ptr(pred), None, n, _ptr(value))
     _check(L.rv_verify_timeline(formula.handle, ctypes.byref(tr), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
                                 _ptr(verd), _ptr(vkey), _ptr(vidx), _ptr(nv), _stream_handle(stream)))
-    k = int(nv.item())
-    keys = vkey[:k].cpu().numpy().view(np.uint64).tolist()
-    idx = vidx[:k].cpu().numpy().view(np.uint32).tolist()
-    return verd[:n].cpu().numpy(), dict(zip(keys, idx))
+    timeline_device.last_out = out
+    return verd[:n], vkey, vidx, int(nv.item())
 
 
 # ---------------------------------------------------------------------- one trace over several ranks

@@ -143,10 +143,10 @@ def test_long_cluster_segments_match_single_launch_and_oracle(rv):
     keys, preds, forms, texts, codes, off = _zipf_head_batch(rv, 6, 1_100_000, 16)
     assert (keys[0] == 77).sum() > 1_000_000
     outs = []
-    for lr in (16384, 65536, -1):
-        _, _, _, _, _, out = _run(rv, torch, forms, keys, preds, off, bucket_records=4096, long_records=lr)
+    for br, lr in ((4096, 16384), (4096, 65536), (4096, -1), (8192, 65536)):
+        _, _, _, _, _, out = _run(rv, torch, forms, keys, preds, off, bucket_records=br, long_records=lr)
         outs.append([(r.status, r.root, r.root_counts, r.n_nodes[0]) for r in out])
-    assert outs[0] == outs[1] == outs[2]
+    assert outs[0] == outs[1] == outs[2] == outs[3]
     out = outs[0]
     for t in range(len(keys)):
         kt = torch.from_numpy(keys[t].view(np.int32)).cuda()
