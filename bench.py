@@ -141,10 +141,15 @@ class Clocks:
                 "samples": len(sm)}
 
 
+# the sources the offline path's kernels are compiled from
+OFFLINE_SOURCES = ("offline.cu", "rv_device.cuh", "valuate.h", "profile.h", "rv_internal.h")
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in sorted(os.listdir(os.path.join(ROOT, "paper_1411_2239_b300", "csrc"))):
+    for f in OFFLINE_SOURCES:
         h.update(open(os.path.join(ROOT, "paper_1411_2239_b300", "csrc", f), "rb").read())
+    h.update(open(os.path.join(ROOT, "include", "rv.h"), "rb").read())
     return h.hexdigest()[:16]
 
 
