@@ -31,7 +31,6 @@ using namespace rvd;
 
 namespace {
 
-constexpr int TW = 8;                 // warps per CTA of the radix passes
 constexpr int TT = 256;               // threads per CTA of the scan
 constexpr int TV = 16;                // events per thread of the scan
 constexpr int TTILE = TT * TV;
@@ -40,22 +39,29 @@ constexpr unsigned TFULL = 0xFFFFFFFFu;
 struct Agg { uint64_t map; uint32_t head, pad; };   // head: a segment starts inside
 
 // ------------------------------------------------------------------ radix passes
+// A pass splits the (key, index) pairs stably by one 8-bit digit.  It works on
+// CTA tiles of RT pairs: k_t_hist counts each tile's digits, k_t_colscan turns
+// the counts into every tile's offset per digit, and k_t_scatter stages its
+// tile in shared memory, orders it by digit there (warps own contiguous
+// slices, lanes of equal digits ranked by ballots), and writes each digit's
+// run contiguously, so the global stores are runs rather than scattered words.
+constexpr int RT = 4096;              // pairs per tile
+constexpr int RTT = 256;              // threads per tile
+constexpr int RTW = RTT / 32;
+
 template <typename K>
-__global__ void __launch_bounds__(TW * 32)
-k_t_hist(const K* key, uint64_t n, uint64_t per_warp, int G_w, int shift, uint32_t* hist) {
-  __shared__ uint32_t cnt[TW][256];
-  const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int gw = blockIdx.x * TW + wl;
-  for (int r = lane; r < 256; r += 32) cnt[wl][r] = 0;
-  __syncwarp();
-  if (gw >= G_w) return;
-  const uint64_t begin = (uint64_t)gw * per_warp, end = min(n, begin + per_warp);
-  for (uint64_t i = begin + lane; i < end; i += 32) atomicAdd(&cnt[wl][(uint32_t)(key[i] >> shift) & 255u], 1u);
-  __syncwarp();
-  for (int r = lane; r < 256; r += 32) hist[(uint64_t)r * G_w + gw] = cnt[wl][r];   // digit-major
+__global__ void __launch_bounds__(RTT) k_t_hist(const K* key, uint64_t n, int shift, uint32_t* hist, int ntiles) {
+  __shared__ uint32_t cnt[256];
+  cnt[threadIdx.x] = 0;
+  __syncthreads();
+  const uint64_t b0 = (uint64_t)blockIdx.x * RT;
+  const int len = (int)min((uint64_t)RT, n - b0);
+  for (int i = threadIdx.x; i < len; i += RTT) atomicAdd(&cnt[(uint32_t)(key[b0 + i] >> shift) & 255u], 1u);
+  __syncthreads();
+  hist[(uint64_t)threadIdx.x * ntiles + blockIdx.x] = cnt[threadIdx.x];   // digit-major
 }
 
-// one CTA per digit value: exclusive prefix of its row over the warp slices
+// one CTA per digit value: exclusive prefix of its row over the tiles
 // (rows are contiguous, the histogram being stored digit-major)
 __global__ void __launch_bounds__(1024) k_t_colscan(uint32_t* hist, int G_w, uint64_t* tot) {
   __shared__ uint64_t wsum[32];
@@ -91,40 +97,113 @@ __global__ void __launch_bounds__(1024) k_t_colscan(uint32_t* hist, int G_w, uin
   if (threadIdx.x == blockDim.x - 1) tot[r] = run;
 }
 
-// stable placement of (key, index) by digit, behind the slice's prefix
+// the digits' segment starts: exclusive scan of their 256 totals (one CTA)
+__global__ void __launch_bounds__(256) k_t_segs(const uint64_t* tot, uint64_t* seg) {
+  __shared__ uint64_t ws[8];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const uint64_t mine = tot[threadIdx.x];
+  uint64_t incl = mine;
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint64_t y = __shfl_up_sync(TFULL, incl, d);
+    if (lane >= d) incl += y;
+  }
+  if (lane == 31) ws[w] = incl;
+  __syncthreads();
+  uint64_t before = 0;
+  for (int q = 0; q < w; ++q) before += ws[q];
+  seg[threadIdx.x] = before + incl - mine;
+}
+
+// lanes whose 8-bit values equal this lane's (invalid lanes form their own group)
+__device__ __forceinline__ uint32_t match8(uint32_t v, bool valid) {
+  const uint32_t vb = __ballot_sync(TFULL, valid);
+  uint32_t m = valid ? vb : ~vb;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const uint32_t bk = __ballot_sync(TFULL, (v >> k) & 1u);
+    m &= ((v >> k) & 1u) ? bk : ~bk;
+  }
+  return m;
+}
+
 template <typename K>
-__global__ void __launch_bounds__(TW * 32)
-k_t_scatter(const K* key, const uint32_t* idx, uint64_t n, uint64_t per_warp, int G_w, int shift,
-            const uint32_t* pre, const uint64_t* tot, K* key_out, uint32_t* idx_out) {
-  __shared__ uint64_t seg[256];
-  __shared__ uint64_t cur[TW][256];
-  if (threadIdx.x == 0) {
-    uint64_t s = 0;
-    for (int r = 0; r < 256; ++r) { seg[r] = s; s += tot[r]; }
+struct RadixShared {
+  K key[RT];
+  uint32_t idx[RT];
+  uint8_t let[RT];
+  uint8_t dig[RT];
+  uint16_t perm[RT];                  // perm[j]: the pair at position j of the digit order
+  uint32_t wcur[RTW][256];
+  uint32_t loc[256];
+  uint64_t gbase[256];
+  uint32_t tsum[RTW];
+};
+
+template <typename K>
+__global__ void __launch_bounds__(RTT)
+k_t_scatter(const K* key, const uint32_t* idx, const uint8_t* let, uint64_t n, int shift, const uint32_t* pre,
+            int ntiles, const uint64_t* seg, K* key_out, uint32_t* idx_out, uint8_t* let_out) {
+  extern __shared__ __align__(16) unsigned char radix_smem[];
+  RadixShared<K>& S = *reinterpret_cast<RadixShared<K>*>(radix_smem);
+  const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t lt = (1u << lane) - 1u;
+  const uint64_t b0 = (uint64_t)blockIdx.x * RT;
+  const int len = (int)min((uint64_t)RT, n - b0);
+  for (int i = threadIdx.x; i < RTW * 256; i += RTT) S.wcur[i / 256][i % 256] = 0;
+  // 1. the tile, staged
+  for (int i = threadIdx.x; i < len; i += RTT) {
+    const K k = key[b0 + i];
+    S.key[i] = k;
+    S.idx[i] = idx ? idx[b0 + i] : (uint32_t)(b0 + i);
+    S.let[i] = let[b0 + i];             // letters travel with their events
+    S.dig[i] = (uint8_t)((uint32_t)(k >> shift) & 255u);
   }
   __syncthreads();
-  const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int gw = blockIdx.x * TW + wl;
-  if (gw >= G_w) return;
-  for (int r = lane; r < 256; r += 32) cur[wl][r] = seg[r] + pre[(uint64_t)r * G_w + gw];
-  __syncwarp();
-  const uint64_t begin = (uint64_t)gw * per_warp, end = min(n, begin + per_warp);
-  const uint32_t lt = (1u << lane) - 1u;
-  for (uint64_t base = begin; base < end; base += 32) {
-    const uint64_t i = base + lane;
-    const bool v = i < end;
-    const K k = v ? key[i] : (K)0;
-    const uint32_t d = v ? ((uint32_t)(k >> shift) & 255u) : 0xFFFFFFFFu;
-    const uint32_t peers = __match_any_sync(TFULL, d);
-    uint64_t pos = 0;
-    if (v) pos = cur[wl][d] + __popc(peers & lt);
-    __syncwarp();
-    if (v && lane == __ffs(peers) - 1) cur[wl][d] += __popc(peers);
-    __syncwarp();
-    if (v) {
-      key_out[pos] = k;
-      idx_out[pos] = idx ? idx[i] : (uint32_t)i;
+  // 2. per-warp counts over contiguous slices
+  const int per = (len + RTW - 1) / RTW;
+  const int w0 = min(len, wl * per), w1 = min(len, w0 + per);
+  for (int i = w0 + lane; i < w1; i += 32) atomicAdd(&S.wcur[wl][S.dig[i]], 1u);
+  __syncthreads();
+  // 3. thread d: offsets of digit d inside the tile and in the output
+  {
+    const int d = threadIdx.x;
+    uint32_t tsum_d = 0;
+    for (int w = 0; w < RTW; ++w) tsum_d += S.wcur[w][d];
+    uint32_t x = tsum_d;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(TFULL, x, o);
+      if (lane >= o) x += y;
     }
+    if (lane == 31) S.tsum[wl] = x;
+    __syncthreads();
+    uint32_t run = x - tsum_d;
+    for (int w = 0; w < wl; ++w) run += S.tsum[w];
+    S.loc[d] = run;
+    S.gbase[d] = seg[d] + pre[(uint64_t)d * ntiles + blockIdx.x];
+    for (int w = 0; w < RTW; ++w) { const uint32_t c = S.wcur[w][d]; S.wcur[w][d] = run; run += c; }
+  }
+  __syncthreads();
+  // 4. stable placement by digit
+  for (int base = w0; base < w1; base += 32) {
+    const int i = base + lane;
+    const bool v = i < w1;
+    const uint32_t d = v ? S.dig[i] : 0u;
+    const uint32_t peers = match8(d, v);
+    uint32_t pos = 0;
+    if (v) pos = S.wcur[wl][d] + __popc(peers & lt);
+    __syncwarp();
+    if (v && lane == __ffs(peers) - 1) S.wcur[wl][d] += __popc(peers);
+    __syncwarp();
+    if (v) S.perm[pos] = (uint16_t)i;
+  }
+  __syncthreads();
+  // 5. each digit's run goes out contiguously
+  for (int j = threadIdx.x; j < len; j += RTT) {
+    const uint32_t i = S.perm[j], d = S.dig[i];
+    const uint64_t o = S.gbase[d] + (j - S.loc[d]);
+    key_out[o] = S.key[i];
+    idx_out[o] = S.idx[i];
+    let_out[o] = S.let[i];
   }
 }
 
@@ -195,13 +274,13 @@ __device__ Agg cta_exscan(Agg mine, int ns, Agg* total) {
 }
 
 template <typename K>
-__device__ __forceinline__ Agg thread_agg(const K* key, const uint32_t* idx, const uint8_t* pred, uint64_t n,
-                                          uint64_t i0, const TimelineTab& tab) {
+__device__ __forceinline__ Agg thread_agg(const K* key, const uint8_t* let, uint64_t n, uint64_t i0,
+                                          const TimelineTab& tab) {
   Agg a{IDENTITY_MAP, 0, 0};
   for (int v = 0; v < TV; ++v) {
     const uint64_t i = i0 + v;
     if (i >= n) break;
-    const uint32_t l = pred[idx[i]];
+    const uint32_t l = let[i];
     const uint64_t m = tab.maps[l < (uint32_t)tab.n_letters ? l : 0];
     if (is_head(key, i)) { a.head = 1; a.map = m; }
     else a.map = apply_map(a.map, m, tab.n_states);
@@ -211,17 +290,16 @@ __device__ __forceinline__ Agg thread_agg(const K* key, const uint32_t* idx, con
 
 template <typename K>
 __global__ void __launch_bounds__(TT)
-k_t_tiles(const K* key, const uint32_t* idx, const uint8_t* pred, uint64_t n, TimelineTab tab, Agg* tiles,
-          unsigned int* err) {
+k_t_tiles(const K* key, const uint8_t* let, uint64_t n, TimelineTab tab, Agg* tiles, unsigned int* err) {
   const uint64_t i0 = (uint64_t)blockIdx.x * TTILE + (uint64_t)threadIdx.x * TV;
   Agg total;
-  const Agg mine = thread_agg(key, idx, pred, n, i0, tab);
+  const Agg mine = thread_agg(key, let, n, i0, tab);
   cta_exscan(mine, tab.n_states, &total);
   if (threadIdx.x == 0) tiles[blockIdx.x] = total;
   bool bad = false;
   for (int v = 0; v < TV; ++v) {
     const uint64_t i = i0 + v;
-    if (i < n && pred[idx[i]] >= (uint32_t)tab.n_letters) bad = true;
+    if (i < n && let[i] >= (uint32_t)tab.n_letters) bad = true;
   }
   if (__any_sync(TFULL, bad) && (threadIdx.x & 31) == 0) atomicOr(err, (unsigned)ERR_LETTER);
 }
@@ -246,11 +324,11 @@ __global__ void __launch_bounds__(TT) k_t_tilescan(Agg* tiles, uint64_t ntiles, 
 
 template <typename K>
 __global__ void __launch_bounds__(TT)
-k_t_emit(const K* key, const uint32_t* idx, const uint8_t* pred, uint64_t n, TimelineTab tab, const Agg* tiles,
+k_t_emit(const K* key, const uint32_t* idx, const uint8_t* let, uint64_t n, TimelineTab tab, const Agg* tiles,
          uint8_t* verdict, uint64_t* vkey, uint32_t* vidx, unsigned long long* nviol) {
   const uint64_t i0 = (uint64_t)blockIdx.x * TTILE + (uint64_t)threadIdx.x * TV;
   Agg total;
-  const Agg mine = thread_agg(key, idx, pred, n, i0, tab);
+  const Agg mine = thread_agg(key, let, n, i0, tab);
   const Agg ex = agg_then(tiles[blockIdx.x], cta_exscan(mine, tab.n_states, &total), tab.n_states);
   // the state before this thread's first event (meaningless if that event is a head)
   uint32_t q = step_state((uint32_t)tab.q0, ex.map);
@@ -259,7 +337,7 @@ k_t_emit(const K* key, const uint32_t* idx, const uint8_t* pred, uint64_t n, Tim
     const uint64_t i = i0 + v;
     if (i >= n) break;
     const uint32_t j = idx[i];
-    const uint32_t l = pred[j];
+    const uint32_t l = let[i];
     const uint64_t m = tab.maps[l < (uint32_t)tab.n_letters ? l : 0];
     const bool head = is_head(key, i);
     if (head) { q = (uint32_t)tab.q0; vprev = 0xFFu; }
@@ -279,17 +357,15 @@ k_t_emit(const K* key, const uint32_t* idx, const uint8_t* pred, uint64_t n, Tim
 struct TPlan {
   uint64_t per_warp, ntiles;
   int G_w;
-  size_t o_k0, o_k1, o_i0, o_i1, o_hist, o_tot, o_tiles, o_orand, o_err, o_letters, total;
+  size_t o_k0, o_k1, o_i0, o_i1, o_l0, o_l1, o_hist, o_tot, o_tiles, o_orand, o_err, o_letters, total;
 };
 
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 TPlan tplan(uint64_t n, int kbytes) {
   TPlan p{};
-  const uint64_t max_w = (uint64_t)rv_num_sms() * 3 * TW;
-  const uint64_t gw = std::max<uint64_t>(1, std::min<uint64_t>((n + 2047) / 2048, max_w));
-  p.per_warp = std::max<uint64_t>(32, ((n + gw - 1) / gw + 31) / 32 * 32);
-  p.G_w = (int)std::max<uint64_t>(1, (n + p.per_warp - 1) / p.per_warp);
+  p.per_warp = RT;
+  p.G_w = (int)std::max<uint64_t>(1, (n + RT - 1) / RT);       // radix tiles
   p.ntiles = std::max<uint64_t>(1, (n + TTILE - 1) / TTILE);
   size_t off = 0;
   auto take = [&](size_t b) { size_t r = off; off = a256(off + b); return r; };
@@ -298,8 +374,10 @@ TPlan tplan(uint64_t n, int kbytes) {
   p.o_k1 = take(m * kbytes);
   p.o_i0 = take(m * 4);
   p.o_i1 = take(m * 4);
+  p.o_l0 = take(m);
+  p.o_l1 = take(m);
   p.o_hist = take((size_t)p.G_w * 256 * 4);
-  p.o_tot = take(256 * 8);
+  p.o_tot = take(512 * 8);                  // digit totals, then segment starts
   p.o_tiles = take(p.ntiles * sizeof(Agg));
   p.o_orand = take(16);
   p.o_err = take(16);
@@ -333,6 +411,7 @@ rv_status run_timeline(const rv_formula* f, const rv_trace* t, unsigned char* ws
   const uint64_t n = t->n;
   K* kbuf[2] = {(K*)(ws + p.o_k0), (K*)(ws + p.o_k1)};
   uint32_t* ibuf[2] = {(uint32_t*)(ws + p.o_i0), (uint32_t*)(ws + p.o_i1)};
+  uint8_t* lbuf[2] = {ws + p.o_l0, ws + p.o_l1};
   uint32_t* hist = (uint32_t*)(ws + p.o_hist);
   uint64_t* tot = (uint64_t*)(ws + p.o_tot);
   Agg* tiles = (Agg*)(ws + p.o_tiles);
@@ -360,18 +439,21 @@ rv_status run_timeline(const rv_formula* f, const rv_trace* t, unsigned char* ws
   TCU(cudaMemcpyAsync(h_orand, orand, 16, cudaMemcpyDeviceToHost, s));
   TCU(cudaStreamSynchronize(s));
   const unsigned long long differ = h_orand[0] ^ h_orand[1];
-  const int grid = (p.G_w + TW - 1) / TW;
+  const int grid = p.G_w;
   const K* cur_k = key;
   const uint32_t* cur_i = nullptr;      // identity permutation before the first pass
+  const uint8_t* cur_l = pred;
   int out = 0;
   for (int shift = 0; shift < (int)sizeof(K) * 8; shift += 8) {
     if (((differ >> shift) & 255ull) == 0) continue;
-    RV_LAUNCH("k_t_hist", k_t_hist<K>, grid, TW * 32, 0, s, cur_k, n, p.per_warp, p.G_w, shift, hist);
+    RV_LAUNCH("k_t_hist", k_t_hist<K>, grid, RTT, 0, s, cur_k, n, shift, hist, p.G_w);
     RV_LAUNCH("k_t_colscan", k_t_colscan, 256, 1024, 0, s, hist, p.G_w, tot);
-    RV_LAUNCH("k_t_scatter", k_t_scatter<K>, grid, TW * 32, 0, s, cur_k, cur_i, n, p.per_warp, p.G_w, shift, hist,
-              tot, kbuf[out], ibuf[out]);
+    RV_LAUNCH("k_t_segs", k_t_segs, 1, 256, 0, s, tot, tot + 256);
+    RV_LAUNCH("k_t_scatter", k_t_scatter<K>, grid, RTT, sizeof(RadixShared<K>), s, cur_k, cur_i, cur_l, n, shift,
+              hist, p.G_w, tot + 256, kbuf[out], ibuf[out], lbuf[out]);
     cur_k = kbuf[out];
     cur_i = ibuf[out];
+    cur_l = lbuf[out];
     out ^= 1;
   }
   if (!cur_i) {                          // every key equal: the trace order is already grouped
@@ -385,9 +467,9 @@ rv_status run_timeline(const rv_formula* f, const rv_trace* t, unsigned char* ws
   tab.n_states = f->n_states;
   tab.q0 = f->q0;
   tab.n_letters = f->n_letters;
-  RV_LAUNCH("k_t_tiles", k_t_tiles<K>, (unsigned)p.ntiles, TT, 0, s, cur_k, cur_i, pred, n, tab, tiles, err);
+  RV_LAUNCH("k_t_tiles", k_t_tiles<K>, (unsigned)p.ntiles, TT, 0, s, cur_k, cur_l, n, tab, tiles, err);
   RV_LAUNCH("k_t_tilescan", k_t_tilescan, 1, TT, 0, s, tiles, p.ntiles, tab.n_states);
-  RV_LAUNCH("k_t_emit", k_t_emit<K>, (unsigned)p.ntiles, TT, 0, s, cur_k, cur_i, pred, n, tab, tiles, verdict,
+  RV_LAUNCH("k_t_emit", k_t_emit<K>, (unsigned)p.ntiles, TT, 0, s, cur_k, cur_i, cur_l, n, tab, tiles, verdict,
             vkey, vidx, nviol);
   TCU(cudaGetLastError());
   unsigned int h_err = 0;
@@ -398,6 +480,15 @@ rv_status run_timeline(const rv_formula* f, const rv_trace* t, unsigned char* ws
 }
 
 }  // namespace
+
+rv_status radix_attrs() {
+  if (cudaFuncSetAttribute(k_t_scatter<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sizeof(RadixShared<uint32_t>)) != cudaSuccess ||
+      cudaFuncSetAttribute(k_t_scatter<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sizeof(RadixShared<uint64_t>)) != cudaSuccess)
+    return rv_fail(RV_ECUDA, "cannot set the radix tile's shared memory");
+  return RV_OK;
+}
 
 extern "C" size_t rv_timeline_workspace_size(const rv_formula* f, uint64_t n) {
   if (!f) return 0;
@@ -420,6 +511,7 @@ extern "C" rv_status rv_verify_timeline(const rv_formula* f, const rv_trace* t, 
   }
   const TPlan p = tplan(t->n, f->key_bits / 8);
   if (ws_bytes < p.total) return rv_fail(RV_ENOMEM, "timeline workspace of %zu bytes, need %zu", ws_bytes, p.total);
+  if (rv_status st = rv_once_per_device(RV_ONCE_EXTRA, &radix_attrs)) return st;
   unsigned long long* nv = (unsigned long long*)n_viol;
   if (f->key_bits == 64)
     return run_timeline<uint64_t>(f, t, (unsigned char*)ws, p, event_verdicts, viol_keys, viol_index, nv, s);
