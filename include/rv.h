@@ -254,9 +254,12 @@ rv_status rv_verify_timeline(const rv_formula* f, const rv_trace* t, void* ws, s
  * key_out (uint32), pred_out (uint8) and ts_out (uint64, may be NULL) are
  * device arrays of `capacity` entries; *n_events (host) receives the number
  * of events; more than capacity returns RV_ENOMEM after writing the first
- * capacity.  ws: device workspace of rv_parse_workspace_size(bytes) bytes.
- * Runs on s and returns when the table is complete.  1..16 rules, names of
- * at most 23 characters.  Errors: RV_EINVAL, RV_ENOMEM, RV_ECUDA. */
+ * capacity.  ws: device workspace of rv_parse_workspace_size(bytes) bytes
+ * (8 bytes per 8 KiB of text plus a few words); text may start at any byte
+ * address (16-byte aligned text is read with wider loads).  Runs on s and
+ * returns when the table is complete.  1..16 rules, names of at most 23
+ * characters.  Errors: RV_EINVAL, RV_ENOMEM, RV_ETIMEOUT (a bounded device
+ * wait between text tiles gave up; the table is then not valid), RV_ECUDA. */
 #define RV_PARSE_MAX_RULES 16
 #define RV_PARSE_NAME_LEN 24
 enum { RV_KEY_ARG0 = 0, RV_KEY_RET = 1 };

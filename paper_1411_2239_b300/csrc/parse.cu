@@ -14,9 +14,14 @@
 // calls, signals, exits and failed calls (RET < 0, when the rule asks for
 // success) are dropped.
 //
-// Steps: newlines counted per tile and scanned, line ends emitted in order;
-// one thread parses each line; kept lines compacted in order by a second
-// count/scan/emit.
+// One kernel, one CTA per 8 KiB tile of text taken in order by a ticket: the
+// tile (with 16 bytes before it and 1 KiB after it) is staged in shared memory
+// with 16-byte loads; its newlines are listed by a block scan; one thread
+// parses each line that starts in the tile; the tile's count of kept lines is
+// chained to the earlier tiles' by a decoupled look-back (bounded waits), and
+// the kept events are written at their place in line order.  The text is read
+// from DRAM once; only a line longer than the staged window is parsed from
+// global memory.
 #include <algorithm>
 #include <cstring>
 
@@ -25,12 +30,19 @@
 
 namespace {
 
-constexpr int PT = 256;               // threads per CTA
-constexpr int PB = 64;                // text bytes per thread in the newline pass
-constexpr int PTILE = PT * PB;        // 16 KiB of text per CTA
-constexpr int LT = PT * 8;            // lines per CTA in the compaction
+constexpr int PT = 128;               // threads per CTA
+constexpr int TB = 8192;              // text bytes owned by one tile
+constexpr int OV = 1024;              // bytes staged after the tile: the end of its last line
+constexpr int WB = 16 + TB + OV;      // staged window: 16 bytes before the tile, the tile, the overhang
+constexpr int CB = TB / PT;           // tile bytes per thread in the newline scan (64)
+constexpr int RREG = 2;               // rounds of lines whose events stay in registers until written
 constexpr int MAX_RULES = RV_PARSE_MAX_RULES;
 constexpr unsigned PFULL = 0xFFFFFFFFu;
+constexpr uint64_t ST_AGG = 1ull << 62;      // tile status: own count published
+constexpr uint64_t ST_INC = 2ull << 62;      // tile status: count of every tile up to this one
+constexpr uint64_t ST_VAL = (1ull << 62) - 1;
+constexpr uint32_t MAX_POLLS = 1u << 22;     // look-back polls of one window before giving up
+constexpr uint32_t PERR_SPIN = 1;
 
 struct Rules {
   char name[MAX_RULES][RV_PARSE_NAME_LEN];
@@ -41,76 +53,24 @@ struct Rules {
   int n;
 };
 
-// newlines in this thread's PB bytes (16-byte loads, byte compares)
-__device__ __forceinline__ uint32_t count_nl(const unsigned char* text, uint64_t bytes, uint64_t b0) {
-  uint32_t c = 0;
-  if (b0 + PB <= bytes && ((uintptr_t)(text + b0) & 15) == 0) {
-    const uint4* p = reinterpret_cast<const uint4*>(text + b0);
-#pragma unroll
-    for (int k = 0; k < PB / 16; ++k) {
-      const uint4 v = p[k];
-      c += __popc(__vcmpeq4(v.x, 0x0A0A0A0Au) & 0x01010101u) + __popc(__vcmpeq4(v.y, 0x0A0A0A0Au) & 0x01010101u) +
-           __popc(__vcmpeq4(v.z, 0x0A0A0A0Au) & 0x01010101u) + __popc(__vcmpeq4(v.w, 0x0A0A0A0Au) & 0x01010101u);
-    }
-  } else {
-    for (uint64_t i = b0; i < min(bytes, b0 + PB); ++i) c += text[i] == '\n';
-  }
-  return c;
+// workspace words after the tile status array
+struct PMisc {
+  uint32_t ticket;     // next tile to take
+  uint32_t err;        // PERR_* bits
+  uint64_t total;      // kept lines of the whole text (written by the last tile)
+};
+
+__device__ __forceinline__ uint64_t ld_relaxed(const uint64_t* p) {
+  uint64_t v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed(uint64_t* p, uint64_t v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-// block-wide exclusive scan of one value per thread; *total = the CTA's sum
-__device__ uint64_t block_exscan(uint64_t x, uint64_t* total) {
-  __shared__ uint64_t ws[PT / 32];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  uint64_t incl = x;
-  for (int d = 1; d < 32; d <<= 1) {
-    const uint64_t y = __shfl_up_sync(PFULL, incl, d);
-    if (lane >= d) incl += y;
-  }
-  if (lane == 31) ws[w] = incl;
-  __syncthreads();
-  uint64_t before = 0, all = 0;
-  for (int v = 0; v < PT / 32; ++v) { if (v < w) before += ws[v]; all += ws[v]; }
-  *total = all;
-  __syncthreads();
-  return before + incl - x;
-}
-
-__global__ void __launch_bounds__(PT) k_p_count(const unsigned char* text, uint64_t bytes, uint64_t* tile_nl) {
-  const uint64_t b0 = (uint64_t)blockIdx.x * PTILE + (uint64_t)threadIdx.x * PB;
-  uint64_t total;
-  block_exscan(count_nl(text, bytes, b0), &total);
-  if (threadIdx.x == 0) tile_nl[blockIdx.x] = total;
-}
-
-// exclusive scan of per-tile counts in place (one CTA, PT per round); total at [n]
-__global__ void __launch_bounds__(PT) k_p_scan(uint64_t* v, uint64_t n) {
-  __shared__ uint64_t carry;
-  if (threadIdx.x == 0) carry = 0;
-  __syncthreads();
-  for (uint64_t b = 0; b < n; b += PT) {
-    const uint64_t i = b + threadIdx.x;
-    const uint64_t x = i < n ? v[i] : 0;
-    uint64_t total;
-    const uint64_t ex = block_exscan(x, &total);
-    const uint64_t c = carry;
-    if (i < n) v[i] = c + ex;
-    __syncthreads();
-    if (threadIdx.x == 0) carry = c + total;
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) v[n] = carry;
-}
-
-// position of every newline, in order
-__global__ void __launch_bounds__(PT) k_p_lines(const unsigned char* text, uint64_t bytes, const uint64_t* tile_base,
-                                                uint64_t* nl_pos) {
-  const uint64_t b0 = (uint64_t)blockIdx.x * PTILE + (uint64_t)threadIdx.x * PB;
-  uint64_t total;
-  uint64_t at = tile_base[blockIdx.x] + block_exscan(count_nl(text, bytes, b0), &total);
-  for (uint64_t i = b0; i < min(bytes, b0 + PB); ++i)
-    if (text[i] == '\n') nl_pos[at++] = i;
-}
+// newline flags of four text bytes: 0x01 in each byte that is '\n'
+__device__ __forceinline__ uint32_t nl4(uint32_t w) { return __vcmpeq4(w, 0x0A0A0A0Au) & 0x01010101u; }
 
 // ------------------------------------------------------------------ one line
 struct Cursor {
@@ -265,73 +225,239 @@ __device__ Parsed parse_line(const Rules& R, const unsigned char* b, const unsig
   return out;
 }
 
-__device__ __forceinline__ void line_span(const unsigned char* text, uint64_t bytes, const uint64_t* nl_pos,
-                                          uint64_t n_nl, uint64_t i, const unsigned char** b, const unsigned char** e) {
-  const uint64_t start = i == 0 ? 0 : nl_pos[i - 1] + 1;
-  const uint64_t stop = i < n_nl ? nl_pos[i] : bytes;
-  *b = text + start;
-  *e = text + stop;
-  if (*e > *b && (*e)[-1] == '\r') --*e;
+struct PShared {
+  uint4 win4[WB / 16];               // text [t0 - 16, t0 + TB + OV), zero past the end of the text
+  uint16_t nl[TB];                   // window offsets of the tile's newlines, in order
+  uint32_t wsum[2][PT / 32];         // per-warp kept counts of one round (two rounds alternate)
+  uint64_t base;                     // kept lines of all earlier tiles
+  uint32_t tile, nnl;
+  int32_t ovend;                     // window offset of the first newline after the tile, or -1
+};
+
+// window offsets [b, e) of line L of the tile; -1 in *e: the line runs past the window
+__device__ __forceinline__ void line_bounds(const PShared& S, int h, uint32_t L, int* b, int* e) {
+  *b = (L == 0 && h) ? 16 : S.nl[L - h] + 1;
+  const uint32_t j = L - h + 1;
+  *e = j < S.nnl ? S.nl[j] : S.ovend;
 }
 
-__global__ void __launch_bounds__(PT) k_p_keep(const unsigned char* text, uint64_t bytes, const uint64_t* nl_pos,
-                                               uint64_t n_nl, uint64_t n_lines, Rules R, uint64_t* tile_keep) {
-  uint64_t kept = 0;
-  const uint64_t l0 = (uint64_t)blockIdx.x * LT + (uint64_t)threadIdx.x * (LT / PT);
-  for (uint64_t i = l0; i < min(n_lines, l0 + LT / PT); ++i) {
-    const unsigned char *b, *e;
-    line_span(text, bytes, nl_pos, n_nl, i, &b, &e);
-    kept += parse_line(R, b, e).keep;
+// the parse of line L; a line past the window is read from global memory
+__device__ Parsed parse_at(const PShared& S, const Rules& R, const unsigned char* text, uint64_t bytes,
+                           uint64_t t0, int h, uint32_t L) {
+  int b, e;
+  line_bounds(S, h, L, &b, &e);
+  const unsigned char* win = reinterpret_cast<const unsigned char*>(S.win4);
+  const unsigned char *pb, *pe;
+  if (e >= 0) {
+    pb = win + b;
+    pe = win + e;
+  } else {
+    uint64_t q = t0 + TB + OV;                 // global position of window offset WB
+    while (q < bytes && text[q] != '\n') ++q;
+    pb = text + (t0 + b - 16);
+    pe = text + q;
   }
-  uint64_t total;
-  block_exscan(kept, &total);
-  if (threadIdx.x == 0) tile_keep[blockIdx.x] = total;
+  if (pe > pb && pe[-1] == '\r') --pe;
+  return parse_line(R, pb, pe);
 }
 
-__global__ void __launch_bounds__(PT) k_p_emit(const unsigned char* text, uint64_t bytes, const uint64_t* nl_pos,
-                                               uint64_t n_nl, uint64_t n_lines, Rules R, const uint64_t* tile_base,
-                                               uint64_t cap, uint32_t* key_out, uint8_t* pred_out, uint64_t* ts_out) {
-  const uint64_t l0 = (uint64_t)blockIdx.x * LT + (uint64_t)threadIdx.x * (LT / PT);
-  uint64_t kept = 0;
-  for (uint64_t i = l0; i < min(n_lines, l0 + LT / PT); ++i) {
-    const unsigned char *b, *e;
-    line_span(text, bytes, nl_pos, n_nl, i, &b, &e);
-    kept += parse_line(R, b, e).keep;
+// rank of this thread's keep bit among the CTA's threads in round r; *round_total: the round's count
+__device__ __forceinline__ uint32_t round_rank(PShared& S, int r, bool keep, uint32_t* round_total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const unsigned m = __ballot_sync(PFULL, keep);
+  if (lane == 0) S.wsum[r & 1][w] = __popc(m);
+  __syncthreads();
+  uint32_t before = 0, all = 0;
+#pragma unroll
+  for (int v = 0; v < PT / 32; ++v) {
+    const uint32_t c = S.wsum[r & 1][v];
+    before += v < w ? c : 0;
+    all += c;
   }
-  uint64_t total;
-  uint64_t at = tile_base[blockIdx.x] + block_exscan(kept, &total);
-  for (uint64_t i = l0; i < min(n_lines, l0 + LT / PT); ++i) {
-    const unsigned char *b, *e;
-    line_span(text, bytes, nl_pos, n_nl, i, &b, &e);
-    const Parsed p = parse_line(R, b, e);
-    if (!p.keep) continue;
-    if (at < cap) {
-      key_out[at] = p.key;
-      pred_out[at] = p.code;
-      if (ts_out) ts_out[at] = p.ts_us;
+  *round_total = all;
+  return before + __popc(m & ((1u << lane) - 1));
+}
+
+__global__ void __launch_bounds__(PT) k_p_parse(const unsigned char* text, uint64_t bytes, Rules R, uint64_t* st,
+                                                PMisc* misc, uint64_t cap, uint32_t* key_out, uint8_t* pred_out,
+                                                uint64_t* ts_out) {
+  __shared__ PShared S;
+  const int tid = threadIdx.x, lane = tid & 31;
+  if (tid == 0) S.tile = atomicAdd(&misc->ticket, 1u);
+  __syncthreads();
+  const uint32_t tile = S.tile;
+  const uint64_t t0 = (uint64_t)tile * TB;
+  const uint64_t tb = min((uint64_t)TB, bytes - t0);           // bytes of the tile inside the text
+  unsigned char* win = reinterpret_cast<unsigned char*>(S.win4);
+
+  // 1. stage [t0 - 16, t0 + TB + OV); before the text's first byte a virtual newline
+  const bool aligned = ((uintptr_t)text & 15) == 0;
+  for (int u = tid; u < WB / 16; u += PT) {
+    const int64_t g = (int64_t)t0 - 16 + 16 * (int64_t)u;
+    if (g < 0) {
+      S.win4[u] = make_uint4(0x0A0A0A0Au, 0x0A0A0A0Au, 0x0A0A0A0Au, 0x0A0A0A0Au);
+    } else if (aligned && (uint64_t)g + 16 <= bytes) {
+      S.win4[u] = *reinterpret_cast<const uint4*>(text + g);
+    } else {
+      for (int k = 0; k < 16; ++k) win[16 * u + k] = (uint64_t)g + k < bytes ? text[g + k] : 0;
     }
-    ++at;
+  }
+  __syncthreads();
+
+  // 2. newlines of the tile, listed in order; the first newline of the overhang
+  uint32_t c = 0;
+  const uint32_t* w32 = reinterpret_cast<const uint32_t*>(win + 16 + tid * CB);
+#pragma unroll
+  for (int k = 0; k < CB / 4; ++k) c += __popc(nl4(w32[k]));
+  // block exclusive scan of c
+  uint32_t incl = c;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t y = __shfl_up_sync(PFULL, incl, d);
+    if (lane >= d) incl += y;
+  }
+  if (lane == 31) S.wsum[0][tid >> 5] = incl;
+  __syncthreads();
+  uint32_t at = incl - c, nnl = 0;
+#pragma unroll
+  for (int v = 0; v < PT / 32; ++v) {
+    at += v < (tid >> 5) ? S.wsum[0][v] : 0;
+    nnl += S.wsum[0][v];
+  }
+#pragma unroll
+  for (int k = 0; k < CB / 4; ++k) {
+    uint32_t m = nl4(w32[k]);
+    while (m) {
+      const int bit = __ffs(m) - 1;
+      S.nl[at++] = (uint16_t)(16 + tid * CB + 4 * k + (bit >> 3));
+      m &= m - 1;
+    }
+  }
+  if (tid < 32) {
+    int32_t found = -1;
+    if (t0 + TB >= bytes) {
+      found = (int32_t)(16 + tb);                              // the text ends in this tile
+    } else {
+      const uint32_t* ov = reinterpret_cast<const uint32_t*>(win + 16 + TB);
+      for (int k = 0; k < OV / 128 && found < 0; ++k) {
+        const uint32_t m = nl4(ov[32 * k + lane]);
+        const unsigned any = __ballot_sync(PFULL, m != 0);
+        if (any) {
+          const int l = __ffs(any) - 1;
+          const uint32_t ml = __shfl_sync(PFULL, m, l);
+          found = 16 + TB + 4 * (32 * k + l) + ((__ffs(ml) - 1) >> 3);
+        }
+      }
+      if (found < 0 && t0 + TB + OV >= bytes) found = (int32_t)(16 + (bytes - t0));   // the text ends in the overhang
+    }
+    if (tid == 0) {
+      S.ovend = found;
+      S.nnl = nnl;
+    }
+  }
+  __syncthreads();
+  // a line starts after each newline at [t0 - 1, t0 + tb - 1)
+  const int h = win[15] == '\n';
+  const uint32_t n_lines = h + nnl - (tb && win[16 + tb - 1] == '\n' ? 1u : 0u);
+  const int rounds = (int)((n_lines + PT - 1) / PT);
+
+  // 3. parse; the first RREG rounds keep their events in registers
+  Parsed keep_p[RREG];
+  uint32_t keep_at[RREG];
+  uint32_t kept = 0, kept_reg = 0;
+  for (int r = 0; r < rounds; ++r) {
+    if (r == RREG) kept_reg = kept;
+    const uint32_t L = (uint32_t)r * PT + tid;
+    Parsed p{0, 0, 0, 0};
+    if (L < n_lines) p = parse_at(S, R, text, bytes, t0, h, L);
+    uint32_t rt;
+    const uint32_t rk = kept + round_rank(S, r, p.keep, &rt);
+#pragma unroll
+    for (int q = 0; q < RREG; ++q)
+      if (q == r) { keep_p[q] = p; keep_at[q] = rk; }
+    kept += rt;
+  }
+
+  // 4. decoupled look-back: kept lines of every earlier tile
+  if (tid < 32) {
+    uint64_t excl = 0;
+    if (tile == 0) {
+      if (lane == 0) st_relaxed(&st[0], ST_INC | kept);
+    } else {
+      if (lane == 0) st_relaxed(&st[tile], ST_AGG | kept);
+      int64_t j = (int64_t)tile - 1;
+      bool gave_up = false;
+      for (;;) {
+        const int64_t idx = j - lane;
+        uint64_t v = idx >= 0 ? ld_relaxed(&st[idx]) : ST_INC;
+        uint32_t polls = 0;
+        while (__any_sync(PFULL, (v >> 62) == 0)) {
+          if (++polls > MAX_POLLS) { gave_up = true; break; }
+          if ((v >> 62) == 0) v = ld_relaxed(&st[idx]);
+        }
+        if (gave_up) break;
+        const unsigned inc = __ballot_sync(PFULL, (v >> 62) == 2);
+        const int stop = inc ? __ffs(inc) - 1 : 31;
+        uint64_t x = lane <= stop ? (v & ST_VAL) : 0;
+#pragma unroll
+        for (int d = 16; d; d >>= 1) x += __shfl_xor_sync(PFULL, x, d);
+        excl += x;
+        if (inc) break;
+        j -= 32;
+      }
+      if (lane == 0) {
+        if (gave_up) atomicOr(&misc->err, PERR_SPIN);
+        st_relaxed(&st[tile], ST_INC | ((excl + kept) & ST_VAL));
+      }
+    }
+    if (lane == 0) {
+      S.base = excl;
+      if (t0 + TB >= bytes) misc->total = excl + kept;
+    }
+  }
+  __syncthreads();
+  const uint64_t base = S.base;
+  uint32_t run = kept_reg;
+
+  // 5. events written in line order
+  for (int r = 0; r < rounds; ++r) {
+    Parsed p{0, 0, 0, 0};
+    uint32_t rk = 0;
+    if (r < RREG) {
+#pragma unroll
+      for (int q = 0; q < RREG; ++q)
+        if (q == r) { p = keep_p[q]; rk = keep_at[q]; }
+    } else {                                   // lines past the registers' rounds are parsed again
+      const uint32_t L = (uint32_t)r * PT + tid;
+      if (L < n_lines) p = parse_at(S, R, text, bytes, t0, h, L);
+      uint32_t rt;
+      rk = run + round_rank(S, r, p.keep, &rt);
+      run += rt;
+    }
+    if (p.keep) {
+      const uint64_t o = base + rk;
+      if (o < cap) {
+        key_out[o] = p.key;
+        pred_out[o] = p.code;
+        if (ts_out) ts_out[o] = p.ts_us;
+      }
+    }
   }
 }
 
 struct PPlan {
-  uint64_t ntiles, max_lines, ltiles;
-  size_t o_tnl, o_nl, o_tkeep, total;
+  uint64_t ntiles;
+  size_t o_st, o_misc, total;
 };
 
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 PPlan pplan(uint64_t bytes) {
   PPlan p{};
-  p.ntiles = std::max<uint64_t>(1, (bytes + PTILE - 1) / PTILE);
-  p.max_lines = bytes + 1;                      // at most one line per byte, plus a last unterminated one
-  p.ltiles = std::max<uint64_t>(1, (p.max_lines + LT - 1) / LT);
-  size_t off = 0;
-  auto take = [&](size_t b) { size_t r = off; off = a256(off + b); return r; };
-  p.o_tnl = take((p.ntiles + 1) * 8);
-  p.o_nl = take(std::max<uint64_t>(bytes, 1) * 8);
-  p.o_tkeep = take((p.ltiles + 1) * 8);
-  p.total = off;
+  p.ntiles = std::max<uint64_t>(1, (bytes + TB - 1) / TB);
+  p.o_st = 0;
+  p.o_misc = a256(p.ntiles * 8);
+  p.total = p.o_misc + a256(sizeof(PMisc));
   return p;
 }
 
@@ -370,35 +496,22 @@ extern "C" rv_status rv_parse_strace(const char* text, uint64_t bytes, const rv_
   *n_events = 0;
   if (bytes == 0) return RV_OK;
   const PPlan p = pplan(bytes);
+  if (p.ntiles > 0x7FFFFFFFull) return rv_fail(RV_EINVAL, "text of %llu bytes: at most 2^31 - 1 tiles of %d bytes",
+                                               (unsigned long long)bytes, TB);
   if (ws_bytes < p.total) return rv_fail(RV_ENOMEM, "parse workspace of %zu bytes, need %zu", ws_bytes, p.total);
   unsigned char* W = (unsigned char*)ws;
-  uint64_t* tnl = (uint64_t*)(W + p.o_tnl);
-  uint64_t* nl = (uint64_t*)(W + p.o_nl);
-  uint64_t* tkeep = (uint64_t*)(W + p.o_tkeep);
-  const unsigned char* T = (const unsigned char*)text;
-  RV_LAUNCH("k_p_count", k_p_count, (unsigned)p.ntiles, PT, 0, s, T, bytes, tnl);
-  RV_LAUNCH("k_p_scan", k_p_scan, 1, PT, 0, s, tnl, p.ntiles);
-  RV_LAUNCH("k_p_lines", k_p_lines, (unsigned)p.ntiles, PT, 0, s, T, bytes, tnl, nl);
-  uint64_t n_nl = 0, last_nl = 0;
-  PCU(cudaMemcpyAsync(&n_nl, tnl + p.ntiles, 8, cudaMemcpyDeviceToHost, s));
-  PCU(cudaStreamSynchronize(s));
-  if (n_nl) {
-    PCU(cudaMemcpyAsync(&last_nl, nl + n_nl - 1, 8, cudaMemcpyDeviceToHost, s));
-    PCU(cudaStreamSynchronize(s));
-  }
-  // a last line without a newline counts too
-  const uint64_t n_lines = n_nl + (n_nl == 0 || last_nl + 1 < bytes ? 1 : 0);
-  const uint64_t ltiles = (n_lines + LT - 1) / LT;
-  RV_LAUNCH("k_p_keep", k_p_keep, (unsigned)ltiles, PT, 0, s, T, bytes, nl, n_nl, n_lines, R, tkeep);
-  RV_LAUNCH("k_p_scan", k_p_scan, 1, PT, 0, s, tkeep, ltiles);
-  RV_LAUNCH("k_p_emit", k_p_emit, (unsigned)ltiles, PT, 0, s, T, bytes, nl, n_nl, n_lines, R, tkeep, capacity,
-            key_out, pred_out, ts_out);
+  uint64_t* st = (uint64_t*)(W + p.o_st);
+  PMisc* misc = (PMisc*)(W + p.o_misc);
+  PCU(cudaMemsetAsync(W, 0, p.total, s));
+  RV_LAUNCH("k_p_parse", k_p_parse, (unsigned)p.ntiles, PT, 0, s, (const unsigned char*)text, bytes, R, st, misc,
+            capacity, key_out, pred_out, ts_out);
   PCU(cudaGetLastError());
-  uint64_t kept = 0;
-  PCU(cudaMemcpyAsync(&kept, tkeep + ltiles, 8, cudaMemcpyDeviceToHost, s));
+  PMisc h{};
+  PCU(cudaMemcpyAsync(&h, misc, sizeof h, cudaMemcpyDeviceToHost, s));
   PCU(cudaStreamSynchronize(s));
-  *n_events = kept;
-  if (kept > capacity) return rv_fail(RV_ENOMEM, "%llu events parsed, capacity %llu: only the first were written",
-                                      (unsigned long long)kept, (unsigned long long)capacity);
+  if (h.err & PERR_SPIN) return rv_fail(RV_ETIMEOUT, "parse: look-back wait gave up");
+  *n_events = h.total;
+  if (h.total > capacity) return rv_fail(RV_ENOMEM, "%llu events parsed, capacity %llu: only the first were written",
+                                         (unsigned long long)h.total, (unsigned long long)capacity);
   return RV_OK;
 }

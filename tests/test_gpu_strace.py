@@ -55,3 +55,51 @@ def test_hand_written_and_edge_lines(rv):
     _check(rv, "1.0 socket(AF_INET, 1, 0) = 5")     # one line, no newline
     key, _, _ = rv.parse_strace("", GPU_RULES)
     assert key.numel() == 0
+
+
+def _pad_line(n):
+    """A dropped line of exactly n bytes before its newline (n >= 4)."""
+    return "1.0 " + "z" * (n - 4)
+
+
+def test_lines_on_tile_edges(rv):
+    """The front end stages text in tiles of 8 KiB: lines that end on the last
+    byte of a tile, start on its first byte, or cross its edge."""
+    ev = ["1.0 socket(AF_INET, SOCK_STREAM, IPPROTO_TCP) = 7", "1.5 recvfrom(7, \"a\", 1, 0, NULL, NULL) = 1"]
+    for shift in list(range(-3, 4)) + [-len(ev[0]) - 1, -len(ev[0])]:
+        pad = 8192 - 1 + shift                       # newline of the pad line at byte 8191 + shift
+        text = "\n".join([_pad_line(pad)] + ev * 300) + "\n"
+        _check(rv, text)
+        _check(rv, text[:-1])
+    # an event line exactly filling one tile, then one exactly filling the next
+    fill = "1.0 sendto(5, \"" + "q" * (8191 - 36) + "\", 1, 0, NULL, 0) = 1"
+    assert len(fill) == 8191
+    _check(rv, "\n".join([fill, fill, ev[1]]))
+
+
+def test_lines_longer_than_the_window(rv):
+    """Lines longer than a tile plus its 1 KiB overhang are parsed from global
+    memory; they may start anywhere in a tile."""
+    long_ev = "2.0 sendto(9, \"" + "L" * 20000 + "\", 20000, 0, NULL, 0) = 20000"
+    long_drop = "2.0 write(1, \"" + "D" * 9500 + "\", 9500) = 9500"
+    short = "3.0 recvfrom(9, \"x\", 1, 0, NULL, NULL) = 1"
+    for lead in (0, 1, 100, 8000, 8191, 8192):
+        text = "\n".join([_pad_line(max(4, lead))] * (lead > 0) + [long_ev, short, long_drop, long_ev] + [short] * 50)
+        _check(rv, text)
+        _check(rv, text + "\n")
+    _check(rv, long_ev)                                 # the whole text one long line, no newline
+
+
+def test_unaligned_text_and_capacity(rv):
+    import torch
+    tr = synth.socket_trace(20_000, 300, n_pending=10, seed=125)
+    text = synth.strace_log(tr, seed=126)
+    raw = torch.frombuffer(bytearray(b"#" + text.encode()), dtype=torch.uint8).cuda()
+    dev = raw[1:]                                       # the text starts one byte past a 16-byte boundary
+    assert dev.data_ptr() % 16 == 1
+    key, pred, ts = rv.parse_strace(dev, GPU_RULES)
+    k, c, t = strace.parse(text, RULES)
+    assert key.cpu().numpy().view(np.uint32).tolist() == [x & 0xFFFFFFFF for x in k]
+    assert pred.cpu().numpy().tolist() == c and ts.cpu().numpy().tolist() == t
+    with pytest.raises(RuntimeError, match="capacity"):
+        rv.parse_strace(text, GPU_RULES, capacity=len(k) - 1)
