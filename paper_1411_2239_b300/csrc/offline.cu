@@ -290,11 +290,12 @@ k_scatter_tile(const void* keyp, const uint8_t* pred, uint64_t n, int nq, int n_
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&acc->err, ERR_LETTER);
 }
 
-// Rank of each lane's bucket b among the records of its warp so far: lanes of
-// equal buckets are matched and the lowest of them advances the warp's
-// counter (equal buckets never share a leader, so no atomics).
+// Rank of each lane's bucket b (< 256) among the records of its warp so far:
+// lanes of equal buckets are matched (one ballot per bit: faster than the
+// hardware match in this kernel, measured) and the lowest of them advances
+// the warp's counter (equal buckets never share a leader, so no atomics).
 __device__ __forceinline__ uint32_t warp_rank(uint32_t b, bool v, uint32_t* cnt, uint32_t lt) {
-  const uint32_t peers = __match_any_sync(FULL, v ? b : 0xFFFFFFFFu);
+  const uint32_t peers = match_bits<8>(v ? b : 0u, v);   // b < 256
   const int ld = __ffs(peers) - 1;
   uint32_t old = 0;
   if (v && (int)(threadIdx.x & 31) == ld) {
