@@ -80,3 +80,20 @@ def test_shard_of_an_empty_trace(rv, torch_cuda):
     pred = torch_cuda.empty(0, dtype=torch_cuda.uint8, device="cuda")
     _, _, _, counts = rv.shard_trace(f, key, pred, 4)
     assert counts.cpu().tolist() == [0, 0, 0, 0]
+
+
+def test_full_size_split_of_the_bench_trace(rv, torch_cuda):
+    """The 1e8-event Zipf socket trace split 8 ways, as the bench times it:
+    every segment holds exactly its rank's events in trace order (against the
+    host form), and the parts verified one after another combine to the
+    unsharded result and to the counts the generator's construction fixes."""
+    import bench
+    w = dict(bench.WORKLOADS["c2"])
+    tr = bench.make_trace(w, 1000 * w["cfg"])
+    f = rv.Formula(w["formula"], tr.codes)
+    got = _split_and_check(rv, torch_cuda, f, tr.key, tr.pred, 8)
+    whole = rv.verify(f, _dev(torch_cuda, tr.key), _dev(torch_cuda, tr.pred))
+    assert got.status == 0
+    assert (got.root, got.root_counts, got.level_counts, got.n_nodes, got.events) == \
+           (whole.root, whole.root_counts, whole.level_counts, whole.n_nodes, whole.events)
+    assert bench.matches(got, bench.expected_counts(dict(w, kind="socket"), tr))

@@ -103,3 +103,20 @@ def test_unaligned_text_and_capacity(rv):
     assert pred.cpu().numpy().tolist() == c and ts.cpu().numpy().tolist() == t
     with pytest.raises(RuntimeError, match="capacity"):
         rv.parse_strace(text, GPU_RULES, capacity=len(k) - 1)
+
+
+def test_full_size_log_equals_its_trace(rv):
+    """The bench's log (a 1e6-event Zipf socket trace, 152 MB of strace text
+    with dropped lines and split calls) parsed on the GPU gives back exactly
+    the events of the trace that wrote it, in order."""
+    import torch
+    import bench
+    tr = synth.socket_trace(1_000_000, 10_000, pending_frac=0.03, zipf_s=1.1, seed=6000)
+    text = synth.strace_log(tr, seed=6001)
+    dev = torch.frombuffer(bytearray(text.encode()), dtype=torch.uint8).cuda()
+    key, pred, ts = rv.parse_strace(dev, GPU_RULES, capacity=tr.n + 16)
+    assert key.numel() == tr.n
+    assert (key.cpu().numpy().view(np.uint32) == tr.key).all()
+    assert (pred.cpu().numpy() == tr.pred).all()
+    t = ts.cpu().numpy()
+    assert (np.diff(t) >= 0).all()

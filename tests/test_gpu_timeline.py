@@ -74,3 +74,66 @@ def test_unquantified_and_tiny_traces(rv):
         key = rng.integers(0, 3, size=n).astype(np.uint32)
         _check(rv, "G(receive -> X !receive)", synth.SOCKET_CODES, key, pred, nq=0)
         _check(rv, C1, synth.SOCKET_CODES, key, pred)
+
+
+def test_full_size_trace_sampled_and_against_offline(rv):
+    """The 1e8-event Zipf socket trace the bench times, in the bench's
+    launch configuration.  Sampled bindings (their whole projections, and the
+    first 400 events of the heaviest sampled binding) against the oracle: one
+    binding's per-event verdicts and first violation depend only on its own
+    events.  Every binding's verdict after its last event against the
+    offline path's verdict of that binding (itself checked against the
+    oracle), for all bindings."""
+    import torch
+    import bench
+    w = dict(bench.WORKLOADS["c2"])
+    tr = bench.make_trace(w, 1000 * w["cfg"])
+    f = rv.Formula(w["formula"], tr.codes)
+    key = _dev(torch, tr.key)
+    pred = _dev(torch, tr.pred)
+    v, first = rv.timeline(f, key, pred)
+    n = tr.n
+    assert len(v) == n
+
+    rng = np.random.default_rng(96)
+    cand = np.unique(tr.key[rng.integers(0, n, size=3000)])
+    mask = np.isin(tr.key, cand)
+    pos = np.flatnonzero(mask)
+    kk = tr.key[pos]
+    order = np.argsort(kk, kind="stable")
+    kk, pos = kk[order], pos[order]
+    starts = np.flatnonzero(np.r_[True, kk[1:] != kk[:-1]])
+    ends = np.r_[starts[1:], len(kk)]
+    sizes = ends - starts
+    short = [i for i in range(len(starts)) if sizes[i] <= 400]
+    picked = [short[i] for i in rng.choice(len(short), size=min(60, len(short)), replace=False)]
+    heavy = int(np.argmax(sizes))
+    checks = [(int(kk[starts[i]]), pos[starts[i]:ends[i]], True) for i in picked]
+    checks.append((int(kk[starts[heavy]]), pos[starts[heavy]:starts[heavy] + 400], False))
+    for k, idx, whole in checks:
+        ov, ofirst = oracle_timeline(w["formula"], Schema(tr.codes), np.full(len(idx), k, dtype=np.uint32),
+                                     tr.pred[idx])
+        assert (v[idx] == ov).all(), (k, int(np.flatnonzero(v[idx] != ov)[0]))
+        if whole:
+            want = int(idx[ofirst[(k,)]]) if (k,) in ofirst else None
+            assert first.get(k) == want, k
+        elif (k,) in ofirst:
+            assert first.get(k) == int(idx[ofirst[(k,)]]), k
+
+    # every binding's last verdict equals its offline verdict
+    kt = key.view(torch.int32).to(torch.int64) & 0xFFFFFFFF
+    uniq, inv = torch.unique(kt, return_inverse=True)
+    last = torch.full((uniq.numel(),), -1, dtype=torch.int64, device="cuda")
+    last.scatter_reduce_(0, inv, torch.arange(n, device="cuda", dtype=torch.int64), reduce="amax")
+    vd = torch.from_numpy(v).cuda()
+    last_v = vd[last].cpu().numpy()
+    off = rv.verify(f, key, pred, want_bindings=True)
+    assert len(off.bindings) == uniq.numel()
+    ok = uniq.cpu().numpy()
+    got = np.array([off.bindings[int(x)] for x in ok], dtype=np.uint8)
+    assert (got == last_v).all(), int(ok[np.flatnonzero(got != last_v)[0]])
+    # F is permanent: a binding's first violation is its first F event, and its last verdict is F
+    fk = np.fromiter(first.keys(), dtype=np.uint64, count=len(first))
+    assert len(first) == int((last_v == 0).sum())
+    assert all(v[j] == 0 for j in list(first.values())[:1000])
+    assert set(fk.tolist()) == set(ok[last_v == 0].tolist())
