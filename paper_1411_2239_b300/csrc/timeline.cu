@@ -241,11 +241,6 @@ __device__ __forceinline__ Agg agg_then(Agg a, Agg b, int ns) {
   return r;
 }
 
-template <typename K>
-__device__ __forceinline__ bool is_head(const K* key, uint64_t i) {
-  return i == 0 || key[i] != key[i - 1];
-}
-
 // inclusive scan of one aggregate per thread over the CTA; returns the
 // exclusive prefix of this thread, and the CTA total in *total
 __device__ Agg cta_exscan(Agg mine, int ns, Agg* total) {
@@ -273,17 +268,73 @@ __device__ Agg cta_exscan(Agg mine, int ns, Agg* total) {
   return agg_then(before, ex, ns);
 }
 
+// A thread's TV consecutive events in registers: keys, letters (four to a
+// word) and, for the emit, trace indices; 16-byte loads when the thread's
+// events are whole and aligned (the radix buffers always are), else one by one.
 template <typename K>
-__device__ __forceinline__ Agg thread_agg(const K* key, const uint8_t* let, uint64_t n, uint64_t i0,
-                                          const TimelineTab& tab) {
+struct Events {
+  K k[TV];
+  uint32_t lw[TV / 4];
+  int cnt;
+  __device__ __forceinline__ uint32_t letter(int v) const { return (lw[v >> 2] >> (8 * (v & 3))) & 0xFFu; }
+};
+
+template <typename K>
+__device__ __forceinline__ void load_events(const K* key, const uint8_t* let, uint64_t n, uint64_t i0, Events<K>& e) {
+  e.cnt = i0 < n ? (int)min((uint64_t)TV, n - i0) : 0;
+  const bool vec = e.cnt == TV && ((((uintptr_t)(key + i0)) | ((uintptr_t)(let + i0))) & 15) == 0;
+  if (vec) {
+    const uint4* kp = reinterpret_cast<const uint4*>(key + i0);
+#pragma unroll
+    for (int q = 0; q < (int)(TV * sizeof(K) / 16); ++q) {
+      const uint4 x = kp[q];
+      if constexpr (sizeof(K) == 4) {
+        e.k[4 * q] = x.x; e.k[4 * q + 1] = x.y; e.k[4 * q + 2] = x.z; e.k[4 * q + 3] = x.w;
+      } else {
+        e.k[2 * q] = (K)x.y << 32 | x.x;
+        e.k[2 * q + 1] = (K)x.w << 32 | x.z;
+      }
+    }
+    const uint4 lx = *reinterpret_cast<const uint4*>(let + i0);
+    e.lw[0] = lx.x; e.lw[1] = lx.y; e.lw[2] = lx.z; e.lw[3] = lx.w;
+  } else {
+#pragma unroll
+    for (int w = 0; w < TV / 4; ++w) e.lw[w] = 0;
+#pragma unroll
+    for (int v = 0; v < TV; ++v) {
+      e.k[v] = v < e.cnt ? key[i0 + v] : (K)0;
+      if (v < e.cnt) e.lw[v >> 2] |= (uint32_t)let[i0 + v] << (8 * (v & 3));
+    }
+  }
+}
+
+// the key before the thread's first event; for event 0 of the trace one
+// that differs from it (so event 0 starts a segment)
+template <typename K>
+__device__ __forceinline__ K key_before(const K* key, uint64_t i0, const Events<K>& e) {
+  return i0 > 0 ? key[i0 - 1] : (K)~e.k[0];
+}
+
+// the letters' maps and the states' labels, staged in shared memory
+struct TabShared {
+  uint64_t maps[RV_MAX_LETTERS];
+  uint8_t labels[RV_MAX_STATES];
+};
+__device__ __forceinline__ void stage_tab(const TimelineTab& tab, TabShared& T) {
+  for (int l = threadIdx.x; l < RV_MAX_LETTERS; l += blockDim.x) T.maps[l] = l < tab.n_letters ? tab.maps[l] : tab.maps[0];
+  if (threadIdx.x < RV_MAX_STATES) T.labels[threadIdx.x] = tab.labels[threadIdx.x];
+}
+
+template <typename K>
+__device__ __forceinline__ Agg thread_agg(const Events<K>& e, K prev, const TabShared& T, int ns) {
   Agg a{IDENTITY_MAP, 0, 0};
+#pragma unroll
   for (int v = 0; v < TV; ++v) {
-    const uint64_t i = i0 + v;
-    if (i >= n) break;
-    const uint32_t l = let[i];
-    const uint64_t m = tab.maps[l < (uint32_t)tab.n_letters ? l : 0];
-    if (is_head(key, i)) { a.head = 1; a.map = m; }
-    else a.map = apply_map(a.map, m, tab.n_states);
+    if (v < e.cnt) {
+      const uint64_t m = T.maps[e.letter(v)];
+      if (e.k[v] != (v ? e.k[v - 1] : prev)) { a.head = 1; a.map = m; }
+      else a.map = apply_map(a.map, m, ns);
+    }
   }
   return a;
 }
@@ -291,16 +342,21 @@ __device__ __forceinline__ Agg thread_agg(const K* key, const uint8_t* let, uint
 template <typename K>
 __global__ void __launch_bounds__(TT)
 k_t_tiles(const K* key, const uint8_t* let, uint64_t n, TimelineTab tab, Agg* tiles, unsigned int* err) {
+  __shared__ TabShared T;
+  stage_tab(tab, T);
   const uint64_t i0 = (uint64_t)blockIdx.x * TTILE + (uint64_t)threadIdx.x * TV;
+  Events<K> e;
+  load_events(key, let, n, i0, e);
+  const K prev = e.cnt ? key_before(key, i0, e) : (K)0;
+  bool bad = false;
+#pragma unroll
+  for (int v = 0; v < TV; ++v)
+    if (v < e.cnt && e.letter(v) >= (uint32_t)tab.n_letters) bad = true;
+  __syncthreads();
   Agg total;
-  const Agg mine = thread_agg(key, let, n, i0, tab);
+  const Agg mine = thread_agg(e, prev, T, tab.n_states);
   cta_exscan(mine, tab.n_states, &total);
   if (threadIdx.x == 0) tiles[blockIdx.x] = total;
-  bool bad = false;
-  for (int v = 0; v < TV; ++v) {
-    const uint64_t i = i0 + v;
-    if (i < n && let[i] >= (uint32_t)tab.n_letters) bad = true;
-  }
   if (__any_sync(TFULL, bad) && (threadIdx.x & 31) == 0) atomicOr(err, (unsigned)ERR_LETTER);
 }
 
@@ -326,30 +382,46 @@ template <typename K>
 __global__ void __launch_bounds__(TT)
 k_t_emit(const K* key, const uint32_t* idx, const uint8_t* let, uint64_t n, TimelineTab tab, const Agg* tiles,
          uint8_t* verdict, uint64_t* vkey, uint32_t* vidx, unsigned long long* nviol) {
+  __shared__ TabShared T;
+  stage_tab(tab, T);
   const uint64_t i0 = (uint64_t)blockIdx.x * TTILE + (uint64_t)threadIdx.x * TV;
+  Events<K> e;
+  load_events(key, let, n, i0, e);
+  const K prev = e.cnt ? key_before(key, i0, e) : (K)0;
+  uint32_t jj[TV];
+  if (e.cnt == TV && ((uintptr_t)(idx + i0) & 15) == 0) {
+    const uint4* ip = reinterpret_cast<const uint4*>(idx + i0);
+#pragma unroll
+    for (int q = 0; q < TV / 4; ++q) {
+      const uint4 x = ip[q];
+      jj[4 * q] = x.x; jj[4 * q + 1] = x.y; jj[4 * q + 2] = x.z; jj[4 * q + 3] = x.w;
+    }
+  } else {
+#pragma unroll
+    for (int v = 0; v < TV; ++v) jj[v] = v < e.cnt ? idx[i0 + v] : 0u;
+  }
+  __syncthreads();
   Agg total;
-  const Agg mine = thread_agg(key, let, n, i0, tab);
+  const Agg mine = thread_agg(e, prev, T, tab.n_states);
   const Agg ex = agg_then(tiles[blockIdx.x], cta_exscan(mine, tab.n_states, &total), tab.n_states);
   // the state before this thread's first event (meaningless if that event is a head)
   uint32_t q = step_state((uint32_t)tab.q0, ex.map);
-  uint32_t vprev = tab.labels[q];
+  uint32_t vprev = T.labels[q];
+#pragma unroll
   for (int v = 0; v < TV; ++v) {
-    const uint64_t i = i0 + v;
-    if (i >= n) break;
-    const uint32_t j = idx[i];
-    const uint32_t l = let[i];
-    const uint64_t m = tab.maps[l < (uint32_t)tab.n_letters ? l : 0];
-    const bool head = is_head(key, i);
-    if (head) { q = (uint32_t)tab.q0; vprev = 0xFFu; }
-    q = step_state(q, m);
-    const uint32_t vd = tab.labels[q];
-    verdict[j] = (uint8_t)vd;
-    if (vd == RV_BOT && vprev != RV_BOT) {       // F is permanent: the binding's first F event
-      const unsigned long long slot = atomicAdd(nviol, 1ull);
-      vkey[slot] = (uint64_t)key[i];
-      vidx[slot] = j;
+    if (v < e.cnt) {
+      const uint64_t m = T.maps[e.letter(v)];
+      if (e.k[v] != (v ? e.k[v - 1] : prev)) { q = (uint32_t)tab.q0; vprev = 0xFFu; }
+      q = step_state(q, m);
+      const uint32_t vd = T.labels[q];
+      verdict[jj[v]] = (uint8_t)vd;
+      if (vd == RV_BOT && vprev != RV_BOT) {       // F is permanent: the binding's first F event
+        const unsigned long long slot = atomicAdd(nviol, 1ull);
+        vkey[slot] = (uint64_t)e.k[v];
+        vidx[slot] = jj[v];
+      }
+      vprev = vd;
     }
-    vprev = vd;
   }
 }
 
