@@ -508,9 +508,10 @@ __global__ void __launch_bounds__(1024) k_scan(const T* in, int P, T* out, T* to
 // Units of the fold.  A bucket longer than half a unit is cut into
 // ceil(len / unit) units; with `pack`, the shorter buckets of one first-level
 // bucket whose starts fall into the same half-unit window share one unit,
-// which is then at most one unit long and holds whole buckets only.  K[b] is
-// the number of units starting at bucket b and uend[b] the end of a shared
-// unit.
+// which is then at most one unit long and holds whole buckets only (a heavy
+// key's own sub-bucket is never shared).  K[b] is the number of units
+// starting at bucket b; uend[b] is the end of the unit a bucket of at most
+// half a unit heads (its own end when it is not shared).
 __global__ void k_count_units(const uint64_t* bstart, int P, int B2, uint64_t unit, int pack, uint32_t* K,
                               uint64_t* uend, int light) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -520,6 +521,7 @@ __global__ void k_count_units(const uint64_t* bstart, int P, int B2, uint64_t un
   const bool own = light && (b & ((1 << B2) - 1)) >= light;
   if (!pack || len > W || own) {
     K[b] = (uint32_t)((len + unit - 1) / unit);
+    uend[b] = s + len;   // read for every bucket of at most half a unit, a heavy key's own included
     return;
   }
   const int first = (b >> B2) << B2, last = first + (light ? light : 1 << B2);
@@ -558,6 +560,13 @@ __global__ void k_emit_tiles(const uint64_t* bstart, int P, uint64_t tile_len, c
   tl.begin = bstart[lo] + j * tile_len;
   tl.end = min(bstart[lo + 1], tl.begin + tile_len);
   if (uend && bstart[lo + 1] - bstart[lo] <= tile_len / 2) tl.end = uend[lo];
+#ifdef RV_CHECKED
+  // a unit lies inside the records and begins at its bucket's start or later
+  if (tl.end < tl.begin || tl.end > g_caps.n || tl.begin < bstart[lo]) {
+    atomicOr(&g_bounds_err, 1u);
+    tl.end = tl.begin;
+  }
+#endif
   if (RV_INB(t, cap)) tiles[t] = tl;
 }
 
@@ -664,13 +673,16 @@ __device__ __forceinline__ int load_heavy(const HeavyDev& hv, uint32_t b1, uint6
   return nh;
 }
 
-// A direct-mapped filter over the low 8 bits of a record key: j + 1 for the
+// A direct-mapped filter over the low HFILT_BITS bits of a record key: j + 1 for the
 // heavy key j that has them, 0 for none, 0xFF when several share them.  Built
 // by one thread; nh <= HMAXC.
+constexpr int HFILT_BITS = 10;         // 1024 entries: a few dozen heavy keys rarely share one
+constexpr int HFILT = 1 << HFILT_BITS;
 __device__ __forceinline__ void build_filter(uint8_t* filt, const uint64_t* hl, int nh) {
-  for (int i = 0; i < 256; ++i) filt[i] = 0;
+  uint32_t* f4 = reinterpret_cast<uint32_t*>(filt);
+  for (int i = 0; i < HFILT / 4; ++i) f4[i] = 0u;
   for (int j = 0; j < nh; ++j) {
-    const int h = (int)(hl[j] & 255u);
+    const int h = (int)(hl[j] & (HFILT - 1));
     filt[h] = filt[h] ? 0xFF : (uint8_t)(j + 1);
   }
 }
@@ -682,7 +694,7 @@ __device__ __forceinline__ uint32_t sub_of(uint64_t rec, int sh, uint32_t P2L, c
   uint32_t sb = (uint32_t)(rec >> sh) & (P2L - 1);
   if (nh == 0) return sb;
   const uint64_t lk = rec >> 8;
-  const uint32_t f = filt[lk & 255u];
+  const uint32_t f = filt[lk & (HFILT - 1)];
   // branch-free for the common cases (no heavy key, one heavy key behind the filter entry)
   const uint32_t j = (f - 1u) & (HMAXC - 1);
   sb = (f - 1u < (uint32_t)nh && hl[j] == lk) ? P2L + j : sb;
@@ -700,7 +712,7 @@ k_hist2(const typename RecT<F>::type* recs, const Tile* tiles, const unsigned in
         uint32_t* hist2, HeavyDev hv) {
   __shared__ uint32_t cnt_all[SC_WARPS][256];
   __shared__ uint64_t hl_all[SC_WARPS][HMAXC];
-  __shared__ uint8_t filt_all[SC_WARPS][256];
+  __shared__ __align__(4) uint8_t filt_all[SC_WARPS][HFILT];
   const uint32_t P2L = 1u << B2;
   const int P2 = hv.hmax ? 2 << B2 : 1 << B2;    // light sub-buckets, then one per heavy key
   const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -841,7 +853,7 @@ k_scatter2(const typename RecT<F>::type* in, const Tile* tiles, const unsigned i
            const uint32_t* pre2, const uint64_t* bstart2, typename RecT<F>::type* out, HeavyDev hv) {
   __shared__ uint32_t cur_all[SC_WARPS][256];
   __shared__ uint64_t hl_all[SC_WARPS][HMAXC];
-  __shared__ uint8_t filt_all[SC_WARPS][256];
+  __shared__ __align__(4) uint8_t filt_all[SC_WARPS][HFILT];
   const uint32_t P2L = 1u << B2;
   const int B2e = hv.hmax ? B2 + 1 : B2;
   const int P2 = 1 << B2e;
@@ -901,7 +913,7 @@ struct Tile2Shared {
   uint32_t loc[256];
   uint64_t gbase[256];
   uint64_t hl[HMAXC];
-  uint8_t filt[256];
+  alignas(4) uint8_t filt[HFILT];
   uint32_t tsum[TB_WARPS];
 };
 

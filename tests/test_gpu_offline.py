@@ -249,6 +249,27 @@ def test_zipf_heads_in_own_sub_buckets(rv, torch_cuda, opts):
     _check(rv, torch_cuda, C1, tr.codes, tr.key, tr.pred, opts=opts)
 
 
+@pytest.mark.parametrize("opts", [{"sub_bucket_bits": 7}, {"sub_bucket_bits": 3}])
+def test_heavy_keys_with_few_records(rv, torch_cuda, opts):
+    # The heavy-key sample reads 8 consecutive events out of every 2048 (every
+    # 256th event on average, for traces under 2^27 events).  Four keys
+    # planted exactly in six of those runs each are counted 48 times, as often
+    # as a key of about 12k events, so each gets a sub-bucket of its own that
+    # holds only its 48 records: at most half a unit, so the unit's end is
+    # taken from the per-bucket unit ends, which must hold it.
+    rng = np.random.default_rng(61)
+    n = 300_000
+    key = rng.choice(rng.integers(0, 2**32, size=30_000, dtype=np.uint64), size=n).astype(np.uint32)
+    planted = rng.integers(0, 2**32, size=4, dtype=np.uint64).astype(np.uint32)
+    for a, k in enumerate(planted):
+        for m in range(6 * a + 3, 6 * a + 9):
+            key[2048 * m: 2048 * m + 8] = k
+    pred = rng.integers(0, 3, size=n).astype(np.uint8)
+    for k in planted:
+        assert (key == k).sum() == 48
+    _check(rv, torch_cuda, C1, synth.SOCKET_CODES, key, pred, opts=opts)
+
+
 def test_many_multi_unit_buckets(rv, torch_cuda):
     # 2^14 light sub-buckets of about 300 records cut into 256-record units:
     # over 8192 buckets are folded by two units or more, so the bucket list of
