@@ -822,11 +822,14 @@ def main():
         return run_sub(args)
     if args.events:
         w = WORKLOADS[args.workload]
-        scale = args.events / w["n"]
-        w["n"] = args.events
-        for k in ("n_ids", "n_users"):
-            if k in w:
-                w[k] = max(10, int(w[k] * scale))
+        if w["kind"] == "batch":       # fewer traces of the same length mix (about 1.3e6 events per trace)
+            w["n_traces"] = max(8, int(round(w["n_traces"] * args.events / 3.3e8)))
+        elif "n" in w:
+            scale = args.events / w["n"]
+            w["n"] = args.events
+            for k in ("n_ids", "n_users"):
+                if k in w:
+                    w[k] = max(10, int(w[k] * scale))
     if args.impl == "reference":
         return run_reference(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))

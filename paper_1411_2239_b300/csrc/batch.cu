@@ -10,9 +10,12 @@
 //
 // map      k_bhist / k_bscan / k_bucket_scan / k_bscatter: each trace gets
 //          2^bits_t buckets by the top bits of mix32(key) (bits_t from its
-//          length and the autotuned target bucket size), so buckets never mix
-//          traces.  Warp tiles never cross a trace boundary and keep private
-//          cursors, so records keep trace order inside each bucket.
+//          length and the autotuned target bucket size, 4 <= bits_t <= 11),
+//          so buckets never mix traces.  A record is 4 bytes: the mixed key's
+//          bits below the bucket's (at most 28, which identify the binding
+//          inside its bucket, mix32 being a bijection) above a 4-bit letter.
+//          Warp tiles never cross a trace boundary and keep private cursors,
+//          so records keep trace order inside each bucket.
 // monitor  k_bfold: per bucket, chunks of records are stably counting-sorted
 //          by binding slot in shared memory; then warps walk the bindings'
 //          letter runs with lane f stepping formula f's monitor (states in
@@ -42,6 +45,7 @@ constexpr int BATCHR = 16;            // load batching
 constexpr int MAXF = 32;              // formulas per trace (one per lane)
 constexpr int MAXL = 16;              // letters per formula in batched mode
 constexpr int MAXBITS = 11;           // at most 2048 buckets per trace
+constexpr int MINBITS = 4;            // at least 16: a record keeps the 28 mixed-key bits below the bucket's
 constexpr int FW = 4;                 // warps per CTA in k_bfold
 constexpr int CHUNK = 4096;           // records sorted at once in k_bfold
 constexpr int BSLOTS = 512;           // bindings per pass over a bucket held in shared memory
@@ -191,7 +195,7 @@ __global__ void __launch_bounds__(1024) k_scan64(const uint64_t* tot, int P, uin
 
 __global__ void __launch_bounds__(BW * 32)
 k_bscatter(BatchDev d, const uint32_t* key, const uint8_t* pred, const uint32_t* pre, const uint64_t* bstart,
-           uint64_t* recs) {
+           uint32_t* recs) {
   __shared__ uint32_t cur_all[BW][1 << MAXBITS];
   const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tile = blockIdx.x * BW + wl;
@@ -205,7 +209,7 @@ k_bscatter(BatchDev d, const uint32_t* key, const uint8_t* pred, const uint32_t*
   const uint32_t lt = lanemask_lt();
   for (uint64_t base = T.begin; base < T.end; base += 32 * BATCHR) {
     uint32_t b[BATCHR];
-    uint64_t r[BATCHR];
+    uint32_t r[BATCHR];
 #pragma unroll
     for (int j = 0; j < BATCHR; ++j) {
       const uint64_t i = base + j * 32 + lane;
@@ -215,8 +219,9 @@ k_bscatter(BatchDev d, const uint32_t* key, const uint8_t* pred, const uint32_t*
         const uint32_t k = key[i];
         uint32_t l = pred[i];
         if (l >= nl) l = 0;
-        b[j] = bucket_of(k, bits);
-        r[j] = ((uint64_t)k << 8) | l;
+        const uint32_t h = mix32(k);
+        b[j] = h >> (32 - bits);
+        r[j] = ((h & (0xFFFFFFFFu >> bits)) << 4) | l;   // the bucket holds the top bits
       }
     }
 #pragma unroll
@@ -260,10 +265,10 @@ struct BFoldShared {
   unsigned int nslots, ovf, next, npass;
 };
 
-// the bindings a pass over a bucket folds: low `bits` bits of the key's mix
-// (the bucket is chosen by its top bits) equal to `val`
-__device__ __forceinline__ bool in_pass(uint32_t key, uint32_t bits, uint32_t val) {
-  return bits == 0 || (mix32(key) & ((1u << bits) - 1u)) == val;
+// the bindings a pass over a bucket folds: low `bits` bits of the binding's
+// record key (the mixed key below the bucket's bits) equal to `val`
+__device__ __forceinline__ bool in_pass(uint32_t rkey, uint32_t bits, uint32_t val) {
+  return bits == 0 || (rkey & ((1u << bits) - 1u)) == val;
 }
 
 // slot of `key` in the bucket's table, inserting it when absent (at most cap
@@ -312,7 +317,7 @@ constexpr unsigned ERR_BUCKET = 32;   // bindings of one bucket collide in every
 // (MAPS = false) or its composed map (MAPS = true).  Returns false when the
 // pass has more than cap bindings (nothing of the table is then valid).
 template <bool MAPS>
-__device__ bool fold_records(BFoldShared& S, const uint64_t* recs, uint64_t r0, uint64_t r1, uint32_t pbits,
+__device__ bool fold_records(BFoldShared& S, const uint32_t* recs, uint64_t r0, uint64_t r1, uint32_t pbits,
                              uint32_t pval, int cap, unsigned int* err) {
   const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31, nthr = FW * 32;
   const uint32_t lt = lanemask_lt();
@@ -320,15 +325,15 @@ __device__ bool fold_records(BFoldShared& S, const uint64_t* recs, uint64_t r0, 
     const int cn = (int)min((uint64_t)CHUNK, r1 - c0);
     // 1. binding slot of every record of the chunk (NO_SLOT: not in this pass)
     for (int i = threadIdx.x; i < cn; i += nthr) {
-      const uint64_t r = recs[c0 + i];
-      const uint32_t key = (uint32_t)(r >> 8);
+      const uint32_t r = recs[c0 + i];
+      const uint32_t key = r >> 4;
       int sl = NO_SLOT;
       if (in_pass(key, pbits, pval)) {
         sl = bfind_or_insert<MAPS>(S, key, cap, err);
         if (sl < 0) sl = 0;
       }
       S.slot_of[i] = (uint16_t)sl;
-      S.letter[i] = (uint8_t)(r & 0xFF);
+      S.letter[i] = (uint8_t)(r & 0xFu);
     }
     for (int i = threadIdx.x; i < FW * BSLOTS; i += nthr) S.wcnt[i / BSLOTS][i % BSLOTS] = 0;
     __syncthreads();
@@ -454,7 +459,7 @@ __global__ void k_bextra(const uint64_t* bstart, int NB, uint64_t long_records, 
 }
 
 __global__ void __launch_bounds__(FW * 32)
-k_bseg(BatchDev d, const uint64_t* recs, const uint64_t* bstart, const uint64_t* item_base, uint64_t long_records,
+k_bseg(BatchDev d, const uint32_t* recs, const uint64_t* bstart, const uint64_t* item_base, uint64_t long_records,
        Slab* slabs, unsigned int* err, unsigned int* next) {
   extern __shared__ __align__(16) unsigned char bsm[];
   BFoldShared& S = *reinterpret_cast<BFoldShared*>(bsm);
@@ -511,7 +516,7 @@ __device__ bool apply_slab(BFoldShared& S, const Slab& sb, uint32_t pbits, uint3
 }
 
 __global__ void __launch_bounds__(FW * 32)
-k_bfold(BatchDev d, const uint64_t* recs, const uint64_t* bstart, const uint64_t* item_base, uint64_t long_records,
+k_bfold(BatchDev d, const uint32_t* recs, const uint64_t* bstart, const uint64_t* item_base, uint64_t long_records,
         const Slab* slabs, unsigned long long* counts, unsigned long long* nbind, unsigned int* err,
         unsigned int* next) {
   extern __shared__ __align__(16) unsigned char bsm[];
@@ -659,7 +664,7 @@ void plan_shape(const rv_batch* b, int bucket_records, int tile_events, std::vec
   size_t hist = 0;
   for (int t = 0; t < b->nt; ++t) {
     const uint64_t len = b->offsets[t + 1] - b->offsets[t];
-    uint32_t k = 0;
+    uint32_t k = MINBITS;
     while (k < (uint32_t)MAXBITS && (len >> k) > (uint64_t)bucket_records) ++k;
     if (bits) bits->push_back(k);
     const uint32_t nb = 1u << k;
@@ -681,7 +686,7 @@ BatchLayout layout(const rv_batch* b, int NB, size_t hist_entries, int long_reco
   L.o_hist = take(std::max<size_t>(hist_entries, 1) * 4);
   L.o_tot = take((size_t)NB * 8);
   L.o_bstart = take((size_t)(NB + 1) * 8);
-  L.o_recs = take(std::max<uint64_t>(n, 1) * 8);
+  L.o_recs = take(std::max<uint64_t>(n, 1) * 4);
   L.o_extra = take((size_t)NB * 8);
   L.o_item = take((size_t)(NB + 1) * 8);
   // every extra segment holds long_records records of its bucket before it
@@ -767,7 +772,7 @@ rv_status enqueue(rv_batch* b, const uint32_t* key, const uint8_t* pred, unsigne
   uint32_t* hist = (uint32_t*)(ws + L.o_hist);
   uint64_t* tot = (uint64_t*)(ws + L.o_tot);
   uint64_t* bstart = (uint64_t*)(ws + L.o_bstart);
-  uint64_t* recs = (uint64_t*)(ws + L.o_recs);
+  uint32_t* recs = (uint32_t*)(ws + L.o_recs);
   unsigned long long* counts = (unsigned long long*)(ws + L.o_counts);
   unsigned long long* nbind = (unsigned long long*)(ws + L.o_nbind);
   unsigned int* err = (unsigned int*)(ws + L.o_err);
