@@ -46,7 +46,7 @@ constexpr int MAXF = 32;              // formulas per trace (one per lane)
 constexpr int MAXL = 16;              // letters per formula in batched mode
 constexpr int MAXBITS = 11;           // at most 2048 buckets per trace
 constexpr int MINBITS = 4;            // at least 16: a record keeps the 28 mixed-key bits below the bucket's
-constexpr int FW = 4;                 // warps per CTA in k_bfold
+constexpr int FW = 8;                 // warps per CTA in k_bfold (three CTAs per SM)
 constexpr int CHUNK = 4096;           // records sorted at once in k_bfold
 constexpr int BSLOTS = 512;           // bindings per pass over a bucket held in shared memory
 constexpr int SSLOTS = 32;            // bindings of a long bucket's segment kept as composed maps
@@ -249,11 +249,13 @@ struct Slab {
 
 struct BFoldShared {
   uint64_t lmap[MAXL][MAXF];
-  uint64_t smap[SSLOTS][MAXF];   // segment maps (long-bucket segments)
+  union {                        // k_bseg composes maps, k_bfold steps states: never both
+    uint64_t smap[SSLOTS][MAXF]; // segment maps (long-bucket segments)
+    uint8_t state[BSLOTS][MAXF];
+  };
   uint8_t labels[MAXF][16];
   uint64_t tkey[BHT];            // key | 1 << 32 once claimed, 0 when empty
   uint16_t tslot[BHT];
-  uint8_t state[BSLOTS][MAXF];
   uint16_t slot_of[CHUNK];
   uint8_t letter[CHUNK];
   uint8_t sorted[CHUNK];
@@ -264,6 +266,9 @@ struct BFoldShared {
   uint32_t pass_bits[MAXPASSBITS + 2], pass_val[MAXPASSBITS + 2];
   unsigned int nslots, ovf, next, npass;
 };
+
+// three fold CTAs of FW warps per SM (228 KB of shared memory, 1 KB reserved per CTA)
+static_assert(3 * (sizeof(BFoldShared) + 1024) <= 228 * 1024, "three batched fold CTAs per SM");
 
 // the bindings a pass over a bucket folds: low `bits` bits of the binding's
 // record key (the mixed key below the bucket's bits) equal to `val`
