@@ -171,7 +171,8 @@ typedef struct {
 /* Tuning knobs; zero means "choose automatically". */
 typedef struct {
   int bucket_bits;       /* log2 of the first-level key buckets, 8..11 */
-  int sub_bucket_bits;   /* log2 of the second-level split, 0..7 */
+  int sub_bucket_bits;   /* log2 of the second-level split, 0..7 (0..8 without heavy-key routing:
+                            two variables, no_heavy) */
   int unit_records;      /* records folded by one CTA, multiple of 256 */
   int no_heavy;          /* nonzero: no own sub-buckets for bindings that a sample of
                             the trace shows to be heavy (one-variable formulas) */
@@ -203,7 +204,7 @@ rv_status rv_verify_trace(const rv_formula* f, const rv_trace* t, int on_device,
  * dev_out->status: RV_EINVAL for a bad trace (predicate code out of range,
  * timestamps decreasing); RV_EAGAIN, for two-quantifier formulas only, when
  * more distinct outer values fell into one key bucket than a fold unit can
- * count (256; the default split uses 2^15 buckets by hash of the outer value,
+ * count (256; the default split uses 2^16 buckets by hash of the outer value,
  * so only keys crafted to collide reach it) -- rerun through rv_verify_trace,
  * which reports it as an error with a message. */
 rv_status rv_verify_trace_async(const rv_formula* f, const rv_trace* t, void* ws, size_t ws_bytes,

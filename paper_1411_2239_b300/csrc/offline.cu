@@ -2106,17 +2106,22 @@ static Plan make_plan(const rv_formula* f, uint64_t n, int host_input, const rv_
   int b1 = o && o->bucket_bits ? o->bucket_bits : 8;
   pl.B1 = std::min(11, std::max(8, b1));
   pl.P1 = 1 << pl.B1;
-  // two variables: the finest split by default, because a fold unit counts
-  // the outer bindings of its bucket in a table of UCAP entries, and only the
-  // finest split keeps the outer values of any natural trace below that
-  // (more than UCAP distinct outer values would have to share 15 hash bits)
+  // A bucket splits into at most 256 sub-buckets: 2^B2 light ones, and as
+  // many again for heavy keys when heavy routing can be on, so B2 <= 7 then
+  // and B2 <= 8 otherwise.  Two variables: the finest split by default,
+  // because a fold unit counts the outer bindings of its bucket in a table of
+  // UCAP entries, and only the finest split keeps the outer values of any
+  // natural trace below that (more than UCAP distinct outer values would have
+  // to share 16 hash bits); it also keeps most sub-buckets within one unit.
+  const bool heavy_ok = pl.F != FMT_K2 && f->n_quant == 1 && !stream && !(o && o->no_heavy);
+  const int b2max = heavy_ok ? 7 : 8;
   int b2 = 0;
   if (o && o->sub_bucket_bits) b2 = o->sub_bucket_bits;
-  else if (pl.F == FMT_K2) b2 = 7;
+  else if (pl.F == FMT_K2) b2 = b2max;
   else while (b2 < 7 && (n >> (pl.B1 + b2)) > 8192) ++b2;
   b2 += extra_b2;
-  pl.B2 = std::min(7, std::max(0, b2));
-  pl.heavy = pl.F != FMT_K2 && f->n_quant == 1 && pl.B2 > 0 && !stream && !(o && o->no_heavy);
+  pl.B2 = std::min(b2max, std::max(0, b2));
+  pl.heavy = heavy_ok && pl.B2 > 0;
   pl.B2e = pl.B2 + (pl.heavy ? 1 : 0);
   pl.hmax = pl.heavy ? std::min(HMAXC, 1 << pl.B2) : 0;
   pl.hstride = std::max<uint64_t>(HSTRIDE, (n >> (HTAB_BITS - 1)) + 1);

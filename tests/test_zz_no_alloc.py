@@ -148,11 +148,11 @@ def test_noalloc_many_outer_values_in_one_first_level_bucket():
 
 
 def test_noalloc_reports_outer_values_crafted_to_collide():
-    # 300 users whose hashes share all 15 bits of the finest split land in one
+    # 300 users whose hashes share all 16 bits of the finest split land in one
     # key bucket: the call is accepted and queued, and the device result says
     # RV_EAGAIN (more outer values than a fold unit counts), as documented
     import torch
-    users = _users_sharing(15, 300, seed=7)
+    users = _users_sharing(16, 300, seed=7)
     k, p = _nested_trace(users, 2, seed=8)
     f = rv.Formula(C3, synth.FILE_CODES, key_bits=64)
     st, got = _noalloc(torch, f, _dev(torch, k), _dev(torch, p))
