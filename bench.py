@@ -656,7 +656,13 @@ def bench_batch(args):
     b = rv.Batch(forms, off)
     ws = torch.empty(b.workspace_size(), dtype=torch.uint8, device="cuda")
     res = torch.empty(b.nt * b.nf * rv.RESULT_BYTES, dtype=torch.uint8, device="cuda")
-    tuned = b.autotune(key, pred, ws, res)
+    if args.batch_shape:               # profiling: a fixed shape instead of the autotuner's
+        br, te, lr = (int(x) for x in args.batch_shape.split(","))
+        tuned = {"bucket_records": br, "tile_events": te, "long_records": lr}
+        b = rv.Batch(forms, off, **tuned)
+        ws = torch.empty(b.workspace_size(), dtype=torch.uint8, device="cuda")
+    else:
+        tuned = b.autotune(key, pred, ws, res)
     for _ in range(args.warmup):
         b.run(key, pred, ws, res)
     torch.cuda.synchronize()
@@ -815,6 +821,8 @@ def main():
     ap.add_argument("--only", action="store_true", help="the headline workload alone (no workloads object)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--batch-shape", default="",
+                    help="batched workload: BUCKET_RECORDS,TILE_EVENTS,LONG_RECORDS instead of autotuning; profiling only")
     ap.add_argument("--events", type=int, default=0,
                     help="shrink the workload to about this many events (ids scale with it); profiling only")
     args = ap.parse_args()
