@@ -46,6 +46,14 @@ constexpr int MAXF = 32;              // formulas per trace (one per lane)
 constexpr int MAXL = 16;              // letters per formula in batched mode
 constexpr int MAXBITS = 11;           // at most 2048 buckets per trace
 constexpr int MINBITS = 4;            // at least 16: a record keeps the 28 mixed-key bits below the bucket's
+// CTAs of the split resident per SM.  Each warp writes its tile's records to
+// up to 2048 bucket positions at once; with more tiles in flight the open,
+// partly written sectors outgrow L2 and cost DRAM read-modify-writes, so the
+// split is launched with enough (unused) dynamic shared memory that no more
+// than this many CTAs fit an SM's 228 KB.
+constexpr int SCATTER_CPS = 4;
+constexpr int SCATTER_STATIC = BW * (1 << MAXBITS) * 4;            // the cursors
+constexpr int SCATTER_PAD = (228 * 1024 / SCATTER_CPS - 1024 - SCATTER_STATIC) / 1024 * 1024;
 constexpr int FW = 8;                 // warps per CTA in k_bfold (three CTAs per SM)
 constexpr int CHUNK = 4096;           // records sorted at once in k_bfold
 constexpr int BSLOTS = 512;           // bindings per pass over a bucket held in shared memory
@@ -793,7 +801,7 @@ rv_status enqueue(rv_batch* b, const uint32_t* key, const uint8_t* pred, unsigne
     RV_LAUNCH("k_bhist", k_bhist, tb, BW * 32, 0, s, d, key, pred, hist, err);
     RV_LAUNCH("k_bscan", k_bscan, (d.NB + 255) / 256, 256, 0, s, d, hist, tot);
     RV_LAUNCH("k_scan64", k_scan64, 1, 1024, 0, s, tot, d.NB, bstart);
-    RV_LAUNCH("k_bscatter", k_bscatter, tb, BW * 32, 0, s, d, key, pred, hist, bstart, recs);
+    RV_LAUNCH("k_bscatter", k_bscatter, tb, BW * 32, SCATTER_PAD, s, d, key, pred, hist, bstart, recs);
     RV_LAUNCH("k_bextra", k_bextra, (d.NB + 255) / 256, 256, 0, s, bstart, d.NB, lr, extra);
     RV_LAUNCH("k_scan64", k_scan64, 1, 1024, 0, s, extra, d.NB, item_base);
     const int grid = std::min(d.NB, num_sms_b() * 4);
@@ -870,9 +878,11 @@ extern "C" size_t rv_batch_workspace_size(const rv_batch* b) {
 }
 
 // the attribute applies to the current device: set it once per device
+static_assert(SCATTER_PAD >= 0, "the split's cursors fit SCATTER_CPS CTAs per SM");
 static rv_status set_bfold_attr() {
   BCU(cudaFuncSetAttribute(k_bfold, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BFoldShared)));
   BCU(cudaFuncSetAttribute(k_bseg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BFoldShared)));
+  BCU(cudaFuncSetAttribute(k_bscatter, cudaFuncAttributeMaxDynamicSharedMemorySize, SCATTER_PAD));
   return RV_OK;
 }
 
