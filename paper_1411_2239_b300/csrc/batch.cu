@@ -8,7 +8,7 @@
 // binding's events are read once for all its formulas (Algorithm 1 with the
 // SortTrace/SpawnMonitors work shared by the formulas of a trace).
 //
-// map      k_bhist / k_bscan / k_bucket_scan / k_bscatter: each trace gets
+// map      k_bhist / k_bscan_a,b,c / k_scan64 / k_bscatter: each trace gets
 //          2^bits_t buckets by the top bits of mix32(key) (bits_t from its
 //          length and the autotuned target bucket size, 4 <= bits_t <= 11),
 //          so buckets never mix traces.  A record is 4 bytes: the mixed key's
@@ -136,25 +136,67 @@ k_bhist(BatchDev d, const uint32_t* key, const uint8_t* pred, uint32_t* hist, un
 }
 
 // one thread per global bucket: exclusive prefix over the tiles of its trace
-__global__ void k_bscan(BatchDev d, uint32_t* hist, uint64_t* tot) {
+// Exclusive prefix of every bucket's counts over the tiles of its trace, in
+// chunks of SCAN_CH tiles so that a long trace's columns are scanned by many
+// threads: per (bucket, chunk) sums, then each bucket's chunk sums scanned,
+// then each chunk's prefixes on top of the earlier chunks'.  Grid y = chunk.
+constexpr int SCAN_CH = 64;
+constexpr int SCAN_R = 16;            // loads of a column issued before their sums
+
+__device__ __forceinline__ bool chunk_of(const BatchDev& d, int g, int c, uint32_t* b, uint32_t* t0, uint32_t* t1) {
+  const uint32_t t = d.bucket_trace[g];
+  *b = g - d.bucket_base[t];
+  const uint32_t first = d.tile_first[t], last = d.tile_first[t + 1];
+  *t0 = first + (uint32_t)c * SCAN_CH;
+  *t1 = min(last, *t0 + SCAN_CH);
+  return *t0 < last;
+}
+
+__global__ void k_bscan_a(BatchDev d, const uint32_t* hist, uint64_t* part) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x, c = blockIdx.y;
+  uint32_t b, t0, t1;
+  if (g >= d.NB || !chunk_of(d, g, c, &b, &t0, &t1)) return;
+  uint64_t sum = 0;
+  for (uint32_t j0 = t0; j0 < t1; j0 += SCAN_R) {
+    uint32_t x[SCAN_R];
+#pragma unroll
+    for (int j = 0; j < SCAN_R; ++j) x[j] = j0 + j < t1 ? hist[d.tiles[j0 + j].hist_off + b] : 0u;
+#pragma unroll
+    for (int j = 0; j < SCAN_R; ++j) sum += x[j];
+  }
+  part[(uint64_t)c * d.NB + g] = sum;
+}
+
+// per bucket: its chunk sums replaced by their exclusive prefix; tot = the bucket's size
+__global__ void k_bscan_b(BatchDev d, uint64_t* part, uint64_t* tot) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= d.NB) return;
   const uint32_t t = d.bucket_trace[g];
-  const uint32_t b = g - d.bucket_base[t];
-  const uint32_t t0 = d.tile_first[t], t1 = d.tile_first[t + 1];
+  const uint32_t nch = (d.tile_first[t + 1] - d.tile_first[t] + SCAN_CH - 1) / SCAN_CH;
   uint64_t run = 0;
-  constexpr int R = 16;
-  for (uint32_t j0 = t0; j0 < t1; j0 += R) {
-    uint32_t x[R];
+  for (uint32_t c = 0; c < nch; ++c) {
+    const uint64_t x = part[(uint64_t)c * d.NB + g];
+    part[(uint64_t)c * d.NB + g] = run;
+    run += x;
+  }
+  tot[g] = run;
+}
+
+__global__ void k_bscan_c(BatchDev d, uint32_t* hist, const uint64_t* part) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x, c = blockIdx.y;
+  uint32_t b, t0, t1;
+  if (g >= d.NB || !chunk_of(d, g, c, &b, &t0, &t1)) return;
+  uint64_t run = part[(uint64_t)c * d.NB + g];
+  for (uint32_t j0 = t0; j0 < t1; j0 += SCAN_R) {
+    uint32_t x[SCAN_R];
 #pragma unroll
-    for (int j = 0; j < R; ++j) x[j] = j0 + j < t1 ? hist[d.tiles[j0 + j].hist_off + b] : 0u;
+    for (int j = 0; j < SCAN_R; ++j) x[j] = j0 + j < t1 ? hist[d.tiles[j0 + j].hist_off + b] : 0u;
 #pragma unroll
-    for (int j = 0; j < R; ++j) {
+    for (int j = 0; j < SCAN_R; ++j) {
       if (j0 + j < t1) hist[d.tiles[j0 + j].hist_off + b] = (uint32_t)run;
       run += x[j];
     }
   }
-  tot[g] = run;
 }
 
 __global__ void __launch_bounds__(1024) k_scan64(const uint64_t* tot, int P, uint64_t* out) {
@@ -650,6 +692,7 @@ struct rv_batch {
   size_t plan_bytes = 0;
   BatchDev dev{};
   size_t hist_entries = 0;
+  int scan_chunks = 1;            // chunks of SCAN_CH tiles of the longest trace
   // captured graph and the arguments it was captured with
   cudaGraphExec_t exec = nullptr;
   const void* g_key = nullptr;
@@ -662,7 +705,7 @@ struct rv_batch {
 namespace {
 
 struct BatchLayout {
-  size_t o_hist, o_tot, o_bstart, o_recs, o_extra, o_item, o_slabs, o_counts, o_nbind, o_err, o_next, o_next2, total;
+  size_t o_hist, o_part, o_tot, o_bstart, o_recs, o_extra, o_item, o_slabs, o_counts, o_nbind, o_err, o_next, o_next2, total;
   uint64_t max_items;
 };
 
@@ -672,11 +715,13 @@ uint64_t long_len(int long_records) { return long_records > 0 ? (uint64_t)long_r
 size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 void plan_shape(const rv_batch* b, int bucket_records, int tile_events, std::vector<uint32_t>* bits,
-                std::vector<WTile>* tiles, int* NB, size_t* hist_entries) {
+                std::vector<WTile>* tiles, int* NB, size_t* hist_entries, int* scan_chunks) {
   int nb_total = 0;
   size_t hist = 0;
+  uint64_t most = 1;
   for (int t = 0; t < b->nt; ++t) {
     const uint64_t len = b->offsets[t + 1] - b->offsets[t];
+    most = std::max<uint64_t>(most, (len + tile_events - 1) / tile_events);
     uint32_t k = MINBITS;
     while (k < (uint32_t)MAXBITS && (len >> k) > (uint64_t)bucket_records) ++k;
     if (bits) bits->push_back(k);
@@ -689,14 +734,16 @@ void plan_shape(const rv_batch* b, int bucket_records, int tile_events, std::vec
   }
   *NB = nb_total;
   *hist_entries = hist;
+  *scan_chunks = (int)((most + SCAN_CH - 1) / SCAN_CH);   // chunks of the trace with the most tiles
 }
 
-BatchLayout layout(const rv_batch* b, int NB, size_t hist_entries, int long_records) {
+BatchLayout layout(const rv_batch* b, int NB, size_t hist_entries, int scan_chunks, int long_records) {
   BatchLayout L{};
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t r = off; off = a256(off + bytes); return r; };
   const uint64_t n = b->offsets.back();
   L.o_hist = take(std::max<size_t>(hist_entries, 1) * 4);
+  L.o_part = take((size_t)NB * scan_chunks * 8);
   L.o_tot = take((size_t)NB * 8);
   L.o_bstart = take((size_t)(NB + 1) * 8);
   L.o_recs = take(std::max<uint64_t>(n, 1) * 4);
@@ -719,7 +766,8 @@ rv_status build_plan(rv_batch* b) {
   std::vector<WTile> tiles;
   int NB = 0;
   size_t hist_entries = 0;
-  plan_shape(b, b->bucket_records, b->tile_events, &bits, &tiles, &NB, &hist_entries);
+  int chunks = 1;
+  plan_shape(b, b->bucket_records, b->tile_events, &bits, &tiles, &NB, &hist_entries, &chunks);
   std::vector<uint32_t> base(b->nt + 1), btrace(NB), tfirst(b->nt + 1);
   int g = 0;
   for (int t = 0; t < b->nt; ++t) {
@@ -733,6 +781,7 @@ rv_status build_plan(rv_batch* b) {
     while (ti < tiles.size() && tiles[ti].trace == (uint32_t)t) ++ti;
   }
   tfirst[b->nt] = (uint32_t)ti;
+  b->scan_chunks = chunks;
   // one device block for every plan array
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t r = off; off = a256(off + bytes); return r; };
@@ -781,9 +830,10 @@ int num_sms_b() { return rv_num_sms(); }
 rv_status enqueue(rv_batch* b, const uint32_t* key, const uint8_t* pred, unsigned char* ws, rv_result* res,
                   cudaStream_t s) {
   const BatchDev& d = b->dev;
-  const BatchLayout L = layout(b, d.NB, b->hist_entries, b->long_records);
+  const BatchLayout L = layout(b, d.NB, b->hist_entries, b->scan_chunks, b->long_records);
   uint32_t* hist = (uint32_t*)(ws + L.o_hist);
   uint64_t* tot = (uint64_t*)(ws + L.o_tot);
+  uint64_t* part = (uint64_t*)(ws + L.o_part);
   uint64_t* bstart = (uint64_t*)(ws + L.o_bstart);
   uint32_t* recs = (uint32_t*)(ws + L.o_recs);
   unsigned long long* counts = (unsigned long long*)(ws + L.o_counts);
@@ -799,7 +849,10 @@ rv_status enqueue(rv_batch* b, const uint32_t* key, const uint8_t* pred, unsigne
   const int tb = (d.ntiles + BW - 1) / BW;
   if (d.ntiles) {
     RV_LAUNCH("k_bhist", k_bhist, tb, BW * 32, 0, s, d, key, pred, hist, err);
-    RV_LAUNCH("k_bscan", k_bscan, (d.NB + 255) / 256, 256, 0, s, d, hist, tot);
+    const dim3 sg((d.NB + 255) / 256, b->scan_chunks);
+    RV_LAUNCH("k_bscan_a", k_bscan_a, sg, 256, 0, s, d, hist, part);
+    RV_LAUNCH("k_bscan_b", k_bscan_b, (d.NB + 255) / 256, 256, 0, s, d, part, tot);
+    RV_LAUNCH("k_bscan_c", k_bscan_c, sg, 256, 0, s, d, hist, part);
     RV_LAUNCH("k_scan64", k_scan64, 1, 1024, 0, s, tot, d.NB, bstart);
     RV_LAUNCH("k_bscatter", k_bscatter, tb, BW * 32, SCATTER_PAD, s, d, key, pred, hist, bstart, recs);
     RV_LAUNCH("k_bextra", k_bextra, (d.NB + 255) / 256, 256, 0, s, bstart, d.NB, lr, extra);
@@ -868,11 +921,11 @@ extern "C" size_t rv_batch_workspace_size(const rv_batch* b) {
   size_t worst = 0;
   for (int br : {256, 512, 1024, 2048, 4096, 8192, b->bucket_records})
     for (int te : {8192, 16384, 32768, b->tile_events}) {
-      int NB = 0;
+      int NB = 0, ch = 1;
       size_t he = 0;
-      plan_shape(b, br, te, nullptr, nullptr, &NB, &he);
+      plan_shape(b, br, te, nullptr, nullptr, &NB, &he, &ch);
       for (int lr : {b->long_records, 16384})
-        worst = std::max(worst, layout(b, NB, he, lr).total);
+        worst = std::max(worst, layout(b, NB, he, ch, lr).total);
     }
   return worst;
 }
@@ -890,7 +943,7 @@ extern "C" rv_status rv_batch_run(rv_batch* b, const uint32_t* key, const uint8_
                                   rv_result* dev_results, cudaStream_t s) {
   if (!b || !ws || !dev_results || (b->offsets.back() && (!key || !pred)))
     return rv_fail(RV_EINVAL, "null argument");
-  const BatchLayout L = layout(b, b->dev.NB, b->hist_entries, b->long_records);
+  const BatchLayout L = layout(b, b->dev.NB, b->hist_entries, b->scan_chunks, b->long_records);
   if (ws_bytes < L.total) return rv_fail(RV_ENOMEM, "workspace of %zu bytes, need %zu", ws_bytes, L.total);
   if (rv_status st = rv_once_per_device(RV_ONCE_BATCH, &set_bfold_attr)) return st;
   if (rv_prof_enabled())   // per-kernel events need eager launches, not a graph replay
