@@ -56,7 +56,25 @@ __global__ void __launch_bounds__(RTT) k_t_hist(const K* key, uint64_t n, int sh
   __syncthreads();
   const uint64_t b0 = (uint64_t)blockIdx.x * RT;
   const int len = (int)min((uint64_t)RT, n - b0);
-  for (int i = threadIdx.x; i < len; i += RTT) atomicAdd(&cnt[(uint32_t)(key[b0 + i] >> shift) & 255u], 1u);
+  // a whole, aligned tile: each thread's keys arrive by 16-byte loads issued
+  // together (one memory round trip, not one per key); counts do not depend
+  // on the order, so thread t takes words t, t + RTT, ...
+  constexpr int PER = RT / RTT;                       // keys per thread
+  constexpr int KW = 16 / sizeof(K);                  // keys per 16-byte word
+  if (len == RT && ((uintptr_t)(key + b0) & 15) == 0) {
+    const uint4* w = reinterpret_cast<const uint4*>(key + b0);
+    uint4 x[PER / KW];
+#pragma unroll
+    for (int q = 0; q < PER / KW; ++q) x[q] = w[q * RTT + threadIdx.x];
+#pragma unroll
+    for (int q = 0; q < PER / KW; ++q) {
+      const K* kk = reinterpret_cast<const K*>(&x[q]);
+#pragma unroll
+      for (int e = 0; e < KW; ++e) atomicAdd(&cnt[(uint32_t)(kk[e] >> shift) & 255u], 1u);
+    }
+  } else {
+    for (int i = threadIdx.x; i < len; i += RTT) atomicAdd(&cnt[(uint32_t)(key[b0 + i] >> shift) & 255u], 1u);
+  }
   __syncthreads();
   hist[(uint64_t)threadIdx.x * ntiles + blockIdx.x] = cnt[threadIdx.x];   // digit-major
 }
@@ -150,13 +168,55 @@ k_t_scatter(const K* key, const uint32_t* idx, const uint8_t* let, uint64_t n, i
   const uint64_t b0 = (uint64_t)blockIdx.x * RT;
   const int len = (int)min((uint64_t)RT, n - b0);
   for (int i = threadIdx.x; i < RTW * 256; i += RTT) S.wcur[i / 256][i % 256] = 0;
-  // 1. the tile, staged
-  for (int i = threadIdx.x; i < len; i += RTT) {
-    const K k = key[b0 + i];
-    S.key[i] = k;
-    S.idx[i] = idx ? idx[b0 + i] : (uint32_t)(b0 + i);
-    S.let[i] = let[b0 + i];             // letters travel with their events
-    S.dig[i] = (uint8_t)((uint32_t)(k >> shift) & 255u);
+  // 1. the tile, staged (letters travel with their events).  A whole tile
+  // whose arrays are 16-byte aligned (the radix buffers always are) arrives
+  // by 16-byte loads all issued before any of them is stored; otherwise one
+  // event at a time.
+  constexpr int KW = 16 / sizeof(K);
+  const bool vec = len == RT && ((((uintptr_t)(key + b0)) | ((uintptr_t)(let + b0)) |
+                                  (idx ? (uintptr_t)(idx + b0) : (uintptr_t)0)) & 15) == 0;
+  if (vec) {
+    const uint4* kw = reinterpret_cast<const uint4*>(key + b0);
+    const uint4* iw = reinterpret_cast<const uint4*>(idx + b0);
+    const uint4* lw = reinterpret_cast<const uint4*>(let + b0);
+    uint4 xk[RT / KW / RTT], xi[RT / 4 / RTT];
+#pragma unroll
+    for (int q = 0; q < RT / KW / RTT; ++q) xk[q] = kw[q * RTT + threadIdx.x];
+    if (idx) {
+#pragma unroll
+      for (int q = 0; q < RT / 4 / RTT; ++q) xi[q] = iw[q * RTT + threadIdx.x];
+    }
+    static_assert(RT / 16 == RTT, "one 16-byte word of letters per thread");
+    const uint4 xl = lw[threadIdx.x];
+    uint4* sk = reinterpret_cast<uint4*>(S.key);
+#pragma unroll
+    for (int q = 0; q < RT / KW / RTT; ++q) {
+      const int wi = q * RTT + threadIdx.x;
+      sk[wi] = xk[q];
+      const K* kk = reinterpret_cast<const K*>(&xk[q]);
+#pragma unroll
+      for (int e = 0; e < KW; ++e) S.dig[wi * KW + e] = (uint8_t)((uint32_t)(kk[e] >> shift) & 255u);
+    }
+    uint4* si = reinterpret_cast<uint4*>(S.idx);
+#pragma unroll
+    for (int q = 0; q < RT / 4 / RTT; ++q) {
+      const int wi = q * RTT + threadIdx.x;
+      if (idx) {
+        si[wi] = xi[q];
+      } else {
+        const uint32_t i0 = (uint32_t)(b0 + 4 * wi);
+        si[wi] = make_uint4(i0, i0 + 1, i0 + 2, i0 + 3);
+      }
+    }
+    reinterpret_cast<uint4*>(S.let)[threadIdx.x] = xl;
+  } else {
+    for (int i = threadIdx.x; i < len; i += RTT) {
+      const K k = key[b0 + i];
+      S.key[i] = k;
+      S.idx[i] = idx ? idx[b0 + i] : (uint32_t)(b0 + i);
+      S.let[i] = let[b0 + i];
+      S.dig[i] = (uint8_t)((uint32_t)(k >> shift) & 255u);
+    }
   }
   __syncthreads();
   // 2. per-warp counts over contiguous slices
@@ -211,10 +271,27 @@ k_t_scatter(const K* key, const uint32_t* idx, const uint8_t* let, uint64_t n, i
 template <typename K>
 __global__ void k_t_bits(const K* key, uint64_t n, unsigned long long* orand) {
   unsigned long long o = 0, a = ~0ull;
-  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-    o |= (unsigned long long)key[i];
-    a &= (unsigned long long)key[i];
+  const uint64_t gt = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x, gs = (uint64_t)gridDim.x * blockDim.x;
+  // the 16-byte words of the aligned middle, four in flight per thread; the
+  // ragged ends one key at a time
+  constexpr int KW = 16 / sizeof(K);
+  const uint64_t head = min(n, (uint64_t)(((16u - ((uint32_t)(uintptr_t)key & 15u)) & 15u) / sizeof(K)));
+  const uint64_t nw = (n - head) / KW;
+  const uint4* w = reinterpret_cast<const uint4*>(key + head);
+  for (uint64_t q0 = gt; q0 < nw; q0 += 4 * gs) {
+    uint4 x[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) x[j] = q0 + j * gs < nw ? w[q0 + j * gs] : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (q0 + j * gs >= nw) continue;
+      const K* kk = reinterpret_cast<const K*>(&x[j]);
+#pragma unroll
+      for (int e = 0; e < KW; ++e) { o |= (unsigned long long)kk[e]; a &= (unsigned long long)kk[e]; }
+    }
   }
+  for (uint64_t i = gt; i < head; i += gs) { o |= (unsigned long long)key[i]; a &= (unsigned long long)key[i]; }
+  for (uint64_t i = head + nw * KW + gt; i < n; i += gs) { o |= (unsigned long long)key[i]; a &= (unsigned long long)key[i]; }
   for (int d = 16; d > 0; d >>= 1) {
     o |= __shfl_xor_sync(TFULL, o, d);
     a &= __shfl_xor_sync(TFULL, a, d);
