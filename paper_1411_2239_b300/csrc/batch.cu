@@ -378,9 +378,21 @@ __device__ bool fold_records(BFoldShared& S, const uint32_t* recs, uint64_t r0, 
   const uint32_t lt = lanemask_lt();
   for (uint64_t c0 = r0; c0 < r1; c0 += CHUNK) {
     const int cn = (int)min((uint64_t)CHUNK, r1 - c0);
-    // 1. binding slot of every record of the chunk (NO_SLOT: not in this pass)
-    for (int i = threadIdx.x; i < cn; i += nthr) {
-      const uint32_t r = recs[c0 + i];
+    // 1. binding slot of every record of the chunk (NO_SLOT: not in this
+    // pass); a thread's records are all loaded before the first is looked up
+    constexpr int RPT = CHUNK / (FW * 32);
+    static_assert(CHUNK % (FW * 32) == 0, "whole rounds of records per chunk");
+    uint32_t rr[RPT];
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+      const int i = q * nthr + threadIdx.x;
+      rr[q] = i < cn ? recs[c0 + i] : 0u;
+    }
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+      const int i = q * nthr + threadIdx.x;
+      if (i >= cn) continue;
+      const uint32_t r = rr[q];
       const uint32_t key = r >> 4;
       int sl = NO_SLOT;
       if (in_pass(key, pbits, pval)) {

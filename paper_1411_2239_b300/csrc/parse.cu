@@ -291,13 +291,28 @@ __global__ void __launch_bounds__(PT) k_p_parse(const unsigned char* text, uint6
   unsigned char* win = reinterpret_cast<unsigned char*>(S.win4);
 
   // 1. stage [t0 - 16, t0 + TB + OV); before the text's first byte a virtual newline
+  // the window's 16-byte words are all loaded before any is stored (one memory
+  // round trip, not one per word); words outside the text, or of unaligned
+  // text, are filled byte by byte
   const bool aligned = ((uintptr_t)text & 15) == 0;
-  for (int u = tid; u < WB / 16; u += PT) {
+  constexpr int NW = WB / 16, WPT = (NW + PT - 1) / PT;
+  uint4 wv[WPT];
+#pragma unroll
+  for (int q = 0; q < WPT; ++q) {
+    const int u = q * PT + tid;
+    const int64_t g = (int64_t)t0 - 16 + 16 * (int64_t)u;
+    wv[q] = u < NW && g >= 0 && aligned && (uint64_t)g + 16 <= bytes ? *reinterpret_cast<const uint4*>(text + g)
+                                                                     : make_uint4(0u, 0u, 0u, 0u);
+  }
+#pragma unroll
+  for (int q = 0; q < WPT; ++q) {
+    const int u = q * PT + tid;
+    if (u >= NW) continue;
     const int64_t g = (int64_t)t0 - 16 + 16 * (int64_t)u;
     if (g < 0) {
       S.win4[u] = make_uint4(0x0A0A0A0Au, 0x0A0A0A0Au, 0x0A0A0A0Au, 0x0A0A0A0Au);
     } else if (aligned && (uint64_t)g + 16 <= bytes) {
-      S.win4[u] = *reinterpret_cast<const uint4*>(text + g);
+      S.win4[u] = wv[q];
     } else {
       for (int k = 0; k < 16; ++k) win[16 * u + k] = (uint64_t)g + k < bytes ? text[g + k] : 0;
     }

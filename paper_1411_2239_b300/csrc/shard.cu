@@ -27,15 +27,11 @@ constexpr int SH_WARPS = 8;
 constexpr int SH_THREADS = SH_WARPS * 32;
 constexpr int SH_MAX_WORLD = 256;
 constexpr unsigned SH_FULL = 0xFFFFFFFFu;
+constexpr int SH_BATCH = 8;           // rounds of 32 events whose loads are issued together
 
 __host__ __device__ __forceinline__ uint32_t shard_rank(uint64_t outer, int world) {
   const uint64_t h = rvd::mix64(outer + 0x9E3779B97F4A7C15ull);
   return (uint32_t)(((h >> 32) * (uint64_t)world) >> 32);
-}
-
-template <typename K>
-__device__ __forceinline__ uint32_t event_rank(const K* key, uint64_t i, int shift, int world) {
-  return shard_rank((uint64_t)key[i] >> shift, world);
 }
 
 // per warp slice: events per destination rank
@@ -49,7 +45,17 @@ k_shard_hist(const K* key, uint64_t n, uint64_t per_warp, int G_w, int shift, in
   __syncwarp();
   if (gw >= G_w) return;
   const uint64_t begin = (uint64_t)gw * per_warp, end = min(n, begin + per_warp);
-  for (uint64_t i = begin + lane; i < end; i += 32) atomicAdd(&cnt[wl][event_rank(key, i, shift, world)], 1u);
+  for (uint64_t base = begin; base < end; base += 32 * SH_BATCH) {
+    K k[SH_BATCH];
+#pragma unroll
+    for (int j = 0; j < SH_BATCH; ++j) {       // all loads first, so that they are in flight together
+      const uint64_t i = base + j * 32 + lane;
+      k[j] = i < end ? key[i] : (K)0;
+    }
+#pragma unroll
+    for (int j = 0; j < SH_BATCH; ++j)
+      if (base + j * 32 + lane < end) atomicAdd(&cnt[wl][shard_rank((uint64_t)k[j] >> shift, world)], 1u);
+  }
   __syncwarp();
   for (int r = lane; r < world; r += 32) hist[(uint64_t)gw * world + r] = cnt[wl][r];
 }
@@ -111,21 +117,36 @@ k_shard_scatter(const K* key, const uint8_t* pred, const uint32_t* ts, const uin
   __syncwarp();
   const uint64_t begin = (uint64_t)gw * per_warp, end = min(n, begin + per_warp);
   const uint32_t lt = (1u << lane) - 1u;
-  for (uint64_t base = begin; base < end; base += 32) {
-    const uint64_t i = base + lane;
-    const bool v = i < end;
-    const uint32_t r = v ? event_rank(key, i, shift, world) : 0xFFFFFFFFu;
-    const uint32_t peers = __match_any_sync(SH_FULL, r);
-    uint64_t pos = 0;
-    if (v) pos = cur[wl][r] + __popc(peers & lt);
-    __syncwarp();
-    if (v && lane == __ffs(peers) - 1) cur[wl][r] += __popc(peers);
-    __syncwarp();
-    if (v) {
-      key_out[pos] = key[i];
-      pred_out[pos] = pred[i];
-      if (ts_out) ts_out[pos] = ts[i];
-      if (value_out) value_out[pos] = value[i];
+  for (uint64_t base0 = begin; base0 < end; base0 += 32 * SH_BATCH) {
+    // the batch's fields are loaded before any of them is placed
+    K k[SH_BATCH];
+    uint8_t pr[SH_BATCH];
+    uint32_t tv[SH_BATCH], vv[SH_BATCH];
+#pragma unroll
+    for (int j = 0; j < SH_BATCH; ++j) {
+      const uint64_t i = base0 + j * 32 + lane;
+      const bool v = i < end;
+      k[j] = v ? key[i] : (K)0;
+      pr[j] = v ? pred[i] : (uint8_t)0;
+      tv[j] = v && ts_out ? ts[i] : 0u;
+      vv[j] = v && value_out ? value[i] : 0u;
+    }
+#pragma unroll
+    for (int j = 0; j < SH_BATCH; ++j) {
+      const bool v = base0 + j * 32 + lane < end;
+      const uint32_t r = v ? shard_rank((uint64_t)k[j] >> shift, world) : 0xFFFFFFFFu;
+      const uint32_t peers = __match_any_sync(SH_FULL, r);
+      uint64_t pos = 0;
+      if (v) pos = cur[wl][r] + __popc(peers & lt);
+      __syncwarp();
+      if (v && lane == __ffs(peers) - 1) cur[wl][r] += __popc(peers);
+      __syncwarp();
+      if (v) {
+        key_out[pos] = k[j];
+        pred_out[pos] = pr[j];
+        if (ts_out) ts_out[pos] = tv[j];
+        if (value_out) value_out[pos] = vv[j];
+      }
     }
   }
 }
