@@ -204,10 +204,22 @@ __device__ __forceinline__ uint32_t cmp_bits(const CmpTab& t, uint32_t v) {
 static __global__ void k_cmp_letters(const uint8_t* pred, const uint32_t* value, uint64_t n, CmpTab t,
                                      uint8_t* out, unsigned int* err, unsigned int bad_bit) {
   bool bad = false;
-  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t code = pred[i];
-    if (code >= (uint32_t)t.n_base) { bad = true; out[i] = 0; continue; }
-    out[i] = (uint8_t)(code + (uint32_t)t.n_base * cmp_bits(t, value[i]));
+  const uint64_t gt = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x, gs = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i0 = gt; i0 < n; i0 += 4 * gs) {
+    uint32_t code[4], val[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {              // four events' loads in flight before any store
+      const uint64_t i = i0 + j * gs;
+      code[j] = i < n ? pred[i] : 0u;
+      val[j] = i < n ? value[i] : 0u;
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint64_t i = i0 + j * gs;
+      if (i >= n) continue;
+      if (code[j] >= (uint32_t)t.n_base) { bad = true; out[i] = 0; continue; }
+      out[i] = (uint8_t)(code[j] + (uint32_t)t.n_base * cmp_bits(t, val[j]));
+    }
   }
   if (__any_sync(0xFFFFFFFFu, bad) && (threadIdx.x & 31) == 0) atomicOr(err, bad_bit);
 }

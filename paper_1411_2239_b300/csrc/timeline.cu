@@ -88,7 +88,13 @@ __global__ void __launch_bounds__(1024) k_t_colscan(uint32_t* hist, int G_w, uin
   const int per = (G_w + blockDim.x - 1) / blockDim.x;
   const int j0 = threadIdx.x * per, j1 = min(G_w, j0 + per);
   uint64_t mine = 0;
-  for (int j = j0; j < j1; ++j) mine += row[j];
+  for (int j = j0; j < j1; j += 8) {            // eight loads in flight before their sums
+    uint32_t x[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) x[e] = j + e < j1 ? row[j + e] : 0u;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) mine += x[e];
+  }
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   uint64_t incl = mine;
   for (int d = 1; d < 32; d <<= 1) {
@@ -107,10 +113,16 @@ __global__ void __launch_bounds__(1024) k_t_colscan(uint32_t* hist, int G_w, uin
   }
   __syncthreads();
   uint64_t run = (w ? wsum[w - 1] : 0) + incl - mine;
-  for (int j = j0; j < j1; ++j) {
-    const uint32_t c = row[j];
-    row[j] = (uint32_t)run;
-    run += c;
+  for (int j = j0; j < j1; j += 8) {
+    uint32_t x[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) x[e] = j + e < j1 ? row[j + e] : 0u;
+#pragma unroll
+    for (int e = 0; e < 8; ++e)
+      if (j + e < j1) {
+        row[j + e] = (uint32_t)run;
+        run += x[e];
+      }
   }
   if (threadIdx.x == blockDim.x - 1) tot[r] = run;
 }
