@@ -137,3 +137,21 @@ def test_full_size_trace_sampled_and_against_offline(rv):
     assert len(first) == int((last_v == 0).sum())
     assert all(v[j] == 0 for j in list(first.values())[:1000])
     assert set(fk.tolist()) == set(ok[last_v == 0].tolist())
+
+
+def test_unaligned_input_arrays(rv):
+    # the radix passes and the scan read 16-byte words where a tile's arrays
+    # are aligned, one event at a time otherwise: a key and a predicate array
+    # starting one element past a 16-byte boundary take the second way in
+    # the first pass
+    import torch
+    tr = synth.socket_trace(70_000, 2_000, pending_frac=0.05, zipf_s=1.1, seed=97)
+    key = torch.from_numpy(np.concatenate([[0], tr.key]).astype(np.uint32).view(np.int32)).cuda()[1:]
+    pred = torch.from_numpy(np.concatenate([[0], tr.pred]).astype(np.uint8)).cuda()[1:]
+    assert key.data_ptr() % 16 == 4 and pred.data_ptr() % 16 == 1
+    for text in (C1, "A s: socket(s) => G(receive -> X !receive)"):
+        f = rv.Formula(text, tr.codes)
+        v, first = rv.timeline(f, key, pred)
+        ov, ofirst = oracle_timeline(text, Schema(tr.codes), tr.key, tr.pred)
+        assert (v == ov).all(), (text, int(np.flatnonzero(v != ov)[0]))
+        assert first == {D[0]: j for D, j in ofirst.items()}, text
