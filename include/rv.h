@@ -324,7 +324,8 @@ rv_status rv_combine_results(const rv_formula* f, const rv_result* parts, int n_
  *     rv_result[nt * nf] land in dev_results after s completes.  The launch
  *     sequence is captured once per argument set and replayed as a graph.
  *     Cluster thresholds: a trace's bindings are hashed into buckets of about
- *     bucket_records records, whose bindings one CTA folds (lane = formula,
+ *     bucket_records records (16 to 2048 buckets per trace, so a short
+ *     trace's buckets are smaller), whose bindings one CTA folds (lane = formula,
  *     in passes of at most 512 bindings each); a bucket longer than
  *     long_records (its runs too long for one CTA) is cut into segments of
  *     long_records records: later segments are folded by CTAs of their own
