@@ -34,6 +34,7 @@ import hashlib
 import json
 import os
 import platform
+import re
 import statistics
 import subprocess
 import sys
@@ -147,11 +148,24 @@ class Clocks:
 OFFLINE_SOURCES = ("offline.cu", "rv_device.cuh", "valuate.h", "profile.h", "rv_internal.h")
 
 
-def kernel_source_hash():
+_COMMENT = re.compile(r'//[^\n]*|/\*.*?\*/|"(?:\\.|[^"\\\n])*"', re.S)
+
+
+def code_only(text):
+    """C/C++/CUDA source without its comments and blank lines (string
+    literals kept), so that a comment edit leaves the hash unchanged."""
+    body = _COMMENT.sub(lambda m: m.group(0) if m.group(0).startswith('"') else " ", text)
+    return "\n".join(ln.rstrip() for ln in body.splitlines() if ln.strip())
+
+
+def kernel_source_hash(read=None):
+    """Hash of the code (not the comments) the offline kernels are built from;
+    ``read(path)`` returns a file's text (default: the working tree)."""
+    read = read or (lambda p: open(os.path.join(ROOT, p)).read())
     h = hashlib.sha256()
     for f in OFFLINE_SOURCES:
-        h.update(open(os.path.join(ROOT, "paper_1411_2239_b300", "csrc", f), "rb").read())
-    h.update(open(os.path.join(ROOT, "include", "rv.h"), "rb").read())
+        h.update(code_only(read("paper_1411_2239_b300/csrc/" + f)).encode())
+    h.update(code_only(read("include/rv.h")).encode())
     return h.hexdigest()[:16]
 
 
