@@ -116,19 +116,22 @@ k_bhist(BatchDev d, const uint32_t* key, const uint8_t* pred, uint32_t* hist, un
   __syncwarp();
   bool bad = false;
   for (uint64_t base = T.begin; base < T.end; base += 32 * BATCHR) {
-    uint32_t b[BATCHR];
+    // all BATCHR rounds' keys and predicates are loaded before any is used,
+    // so a lane waits for one memory round trip per batch, not per round
+    uint32_t k[BATCHR], l[BATCHR];
 #pragma unroll
     for (int j = 0; j < BATCHR; ++j) {
       const uint64_t i = base + j * 32 + lane;
-      b[j] = EMPTY32;
-      if (i < T.end) {
-        b[j] = bucket_of(key[i], bits);
-        if (pred[i] >= nl) bad = true;
-      }
+      k[j] = i < T.end ? key[i] : 0u;
+      l[j] = i < T.end ? (uint32_t)pred[i] : 0u;
     }
 #pragma unroll
-    for (int j = 0; j < BATCHR; ++j)
-      if (b[j] != EMPTY32) atomicAdd(&cnt[b[j]], 1u);
+    for (int j = 0; j < BATCHR; ++j) {
+      if (base + j * 32 + lane < T.end) {
+        atomicAdd(&cnt[bucket_of(k[j], bits)], 1u);
+        if (l[j] >= nl) bad = true;
+      }
+    }
   }
   if (__any_sync(FULL, bad) && lane == 0) atomicOr(err, (unsigned)ERR_LETTER);
   __syncwarp();
@@ -254,24 +257,48 @@ k_bscatter(BatchDev d, const uint32_t* key, const uint8_t* pred, const uint32_t*
   const uint32_t bits = d.trace_bits[T.trace], nl = d.nletters[T.trace];
   const uint32_t gb = d.bucket_base[T.trace];
   uint32_t* cur = cur_all[wl];
-  for (uint32_t b = lane; b < T.nb; b += 32) cur[b] = (uint32_t)(bstart[gb + b] + pre[T.hist_off + b]);
+  // the tile's cursors: eight bucket starts and offsets per lane in flight
+  // before any cursor is stored
+  constexpr int CB = 8;
+  for (uint32_t c0 = 0; c0 < T.nb; c0 += 32 * CB) {
+    uint64_t bs[CB];
+    uint32_t po[CB];
+#pragma unroll
+    for (int j = 0; j < CB; ++j) {
+      const uint32_t b = c0 + j * 32 + lane;
+      bs[j] = b < T.nb ? bstart[gb + b] : 0ull;
+      po[j] = b < T.nb ? pre[T.hist_off + b] : 0u;
+    }
+#pragma unroll
+    for (int j = 0; j < CB; ++j) {
+      const uint32_t b = c0 + j * 32 + lane;
+      if (b < T.nb) cur[b] = (uint32_t)(bs[j] + po[j]);
+    }
+  }
   __syncwarp();
   const uint32_t lt = lanemask_lt();
   for (uint64_t base = T.begin; base < T.end; base += 32 * BATCHR) {
     uint32_t b[BATCHR];
     uint32_t r[BATCHR];
+    // all BATCHR rounds' keys and predicates are loaded before any is used
 #pragma unroll
     for (int j = 0; j < BATCHR; ++j) {
       const uint64_t i = base + j * 32 + lane;
-      b[j] = EMPTY32;
-      r[j] = 0;
+      r[j] = i < T.end ? key[i] : 0u;
+      b[j] = i < T.end ? (uint32_t)pred[i] : 0u;
+    }
+#pragma unroll
+    for (int j = 0; j < BATCHR; ++j) {
+      const uint64_t i = base + j * 32 + lane;
       if (i < T.end) {
-        const uint32_t k = key[i];
-        uint32_t l = pred[i];
+        uint32_t l = b[j];
         if (l >= nl) l = 0;
-        const uint32_t h = mix32(k);
+        const uint32_t h = mix32(r[j]);
         b[j] = h >> (32 - bits);
         r[j] = ((h & (0xFFFFFFFFu >> bits)) << 4) | l;   // the bucket holds the top bits
+      } else {
+        b[j] = EMPTY32;
+        r[j] = 0;
       }
     }
 #pragma unroll
