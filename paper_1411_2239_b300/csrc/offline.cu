@@ -675,16 +675,34 @@ __device__ __forceinline__ int load_heavy(const HeavyDev& hv, uint32_t b1, uint6
 
 // A direct-mapped filter over the low HFILT_BITS bits of a record key: j + 1 for the
 // heavy key j that has them, 0 for none, 0xFF when several share them.  Built
-// by one thread; nh <= HMAXC.
+// by the 32 lanes of one warp together (all of them call it); nh <= HMAXC.
 constexpr int HFILT_BITS = 10;         // 1024 entries: a few dozen heavy keys rarely share one
 constexpr int HFILT = 1 << HFILT_BITS;
-__device__ __forceinline__ void build_filter(uint8_t* filt, const uint64_t* hl, int nh) {
+__device__ __forceinline__ void build_filter(uint8_t* filt, const uint64_t* hl, int nh, int lane) {
+  static_assert(HMAXC % 32 == 0, "whole rounds of heavy keys");
+  constexpr int R = HMAXC / 32;
   uint32_t* f4 = reinterpret_cast<uint32_t*>(filt);
-  for (int i = 0; i < HFILT / 4; ++i) f4[i] = 0u;
-  for (int j = 0; j < nh; ++j) {
-    const int h = (int)(hl[j] & (HFILT - 1));
-    filt[h] = filt[h] ? 0xFF : (uint8_t)(j + 1);
+  for (int i = lane; i < HFILT / 4; i += 32) f4[i] = 0u;
+  __syncwarp();
+  // every key writes its number at its entry (of several keys at one entry,
+  // one write remains); a key that then finds another number there marks
+  // the entry shared
+  int h[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int j = r * 32 + lane;
+    h[r] = j < nh ? (int)(hl[j] & (HFILT - 1)) : -1;
+    if (h[r] >= 0) filt[h[r]] = (uint8_t)(j + 1);
   }
+  __syncwarp();
+  bool shared_entry[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) shared_entry[r] = h[r] >= 0 && filt[h[r]] != (uint8_t)(r * 32 + lane + 1);
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+    if (shared_entry[r]) filt[h[r]] = 0xFF;
+  __syncwarp();
 }
 
 // second-level sub-bucket of a record: its own for a heavy key (P2L + j),
@@ -723,8 +741,7 @@ k_hist2(const typename RecT<F>::type* recs, const Tile* tiles, const unsigned in
   const Tile tl = tiles[tile];
   const int nh = load_heavy(hv, tl.bucket, hl_all[wl], lane, 32);
   __syncwarp();
-  if (nh && lane == 0) build_filter(filt_all[wl], hl_all[wl], nh);
-  __syncwarp();
+  if (nh) build_filter(filt_all[wl], hl_all[wl], nh, lane);
   const uint64_t* hl = hl_all[wl];
   const uint8_t* filt = filt_all[wl];
   const int sh = sub_shift<F>(B1, B2);
@@ -862,12 +879,27 @@ k_scatter2(const typename RecT<F>::type* in, const Tile* tiles, const unsigned i
   if (tile >= *n_tiles) return;
   const Tile tl = tiles[tile];
   uint32_t* cur = cur_all[wl];
-  for (int b = lane; b < P2; b += 32)
-    cur[b] = (uint32_t)(bstart2[((uint64_t)tl.bucket << B2e) + b] + pre2[(uint64_t)tile * P2 + b]);
+  {
+    // the tile's cursors (P2 <= 256: at most eight per lane), all loaded
+    // before any is stored
+    constexpr int CB = 8;
+    uint64_t bs[CB];
+    uint32_t po[CB];
+#pragma unroll
+    for (int j = 0; j < CB; ++j) {
+      const int b = j * 32 + lane;
+      bs[j] = b < P2 ? bstart2[((uint64_t)tl.bucket << B2e) + b] : 0ull;
+      po[j] = b < P2 ? pre2[(uint64_t)tile * P2 + b] : 0u;
+    }
+#pragma unroll
+    for (int j = 0; j < CB; ++j) {
+      const int b = j * 32 + lane;
+      if (b < P2) cur[b] = (uint32_t)(bs[j] + po[j]);
+    }
+  }
   const int nh = load_heavy(hv, tl.bucket, hl_all[wl], lane, 32);
   __syncwarp();
-  if (nh && lane == 0) build_filter(filt_all[wl], hl_all[wl], nh);
-  __syncwarp();
+  if (nh) build_filter(filt_all[wl], hl_all[wl], nh, lane);
   const uint64_t* hl = hl_all[wl];
   const uint8_t* filt = filt_all[wl];
   const int sh = sub_shift<F>(B1, B2);
@@ -937,7 +969,7 @@ k_scatter2_tile(const typename RecT<F>::type* in, const Tile* tiles, const unsig
   for (int i = threadIdx.x; i < TB_WARPS * 256; i += TB_THREADS) S.wcur[i / 256][i % 256] = 0;
   const int nh = load_heavy(hv, tl.bucket, S.hl, threadIdx.x, TB_THREADS);
   __syncthreads();
-  if (nh && threadIdx.x == 0) build_filter(S.filt, S.hl, nh);
+  if (nh && threadIdx.x < 32) build_filter(S.filt, S.hl, nh, (int)threadIdx.x);
   __syncthreads();
   const int sh = sub_shift<F>(B1, B2);
   const int w0 = wl * PER;
