@@ -169,3 +169,41 @@ def test_autotune_reports_thresholds(rv):
     b.run(k, p, ws, res)
     torch.cuda.synchronize()
     assert [(r.root, r.root_counts) for r in b.results(res)] == [(r.root, r.root_counts) for r in out]
+
+
+SMALL = ["E_{>=6} x: p(x) => (((!p3) U (p3)) U (X(p3))) -> ((G(p3)) -> ((p2) U (!p3)))",
+         "E_{<7} x: p(x) => (F(p2)) -> (F(p0))",
+         "A_{>=85%} x: p(x) => ((X(p0)) -> (X(p3))) U (X(G(p2)))",
+         "A_{=100%} x: p(x) => X(X(G(p1)))",
+         "E_{>6} x: p(x) => ((F(X(p2))) -> (G((p0) U (!p0)))) -> (X(F((p0) U (p1))))",
+         "A_{<75%} x: p(x) => X((((p1) && (p3)) U ((p2) -> (p3))) && ((G(p1)) U (F(!p0))))"]
+LARGE = ["A_{>75%} x: p(x) => ((((p1) -> (p3)) U ((!p3) && (p0))) && (X((!p3) -> (!p2)))) U (X(X((p1) && (p1))))",
+         "A_{<15%} x: p(x) => (X(G(F(p2)))) -> (X(X(X(p2))))"]
+
+
+def test_small_and_large_monitor_traces(rv):
+    # traces whose monitors all have at most 8 states (every map target in
+    # the low word of the nibble map) and traces that mix in monitors of 9
+    # and 12 states, with runs of full and partial rounds of 32 letters and
+    # two bucket sizes: every (trace, formula) against the oracle
+    import torch
+    codes = ["p0", "p1", "p2", "p3"]
+    sets = [SMALL + SMALL[:2], SMALL[:6] + LARGE, LARGE + SMALL[2:] + SMALL[:2], SMALL[::-1] + SMALL[:2]]
+    assert all(len(s) == 8 for s in sets)
+    forms = [[rv.Formula(t, codes) for t in s] for s in sets]
+    assert all(f.n_states <= 8 for f in forms[0]) and all(f.n_states <= 8 for f in forms[3])
+    assert any(f.n_states > 8 for f in forms[1]) and any(f.n_states > 8 for f in forms[2])
+    rng = np.random.default_rng(11)
+    shape = [(40_000, 300), (40_000, 300), (30_000, 3_000), (30_000, 3_000)]   # ~130 and ~10 events a key
+    keys = [rng.integers(0, nk, size=n).astype(np.uint32) * np.uint32(2654435761) for n, nk in shape]
+    preds = [rng.integers(0, 4, size=n).astype(np.uint8) for n, _ in shape]
+    off = np.zeros(len(keys) + 1, dtype=np.uint64)
+    off[1:] = np.cumsum([len(k) for k in keys])
+    for br in (4096, 512):
+        _, _, _, _, _, out = _run(rv, torch, forms, keys, preds, off, bucket_records=br)
+        for t in range(len(keys)):
+            for j, text in enumerate(sets[t]):
+                o = oracle_verify(text, Schema(codes), keys[t], preds[t])
+                r = out[t * 8 + j]
+                assert r.status == 0 and r.root == o.root and r.root_counts == o.root_counts, (br, t, j, text)
+                assert r.n_nodes[0] == o.n_nodes[0]
