@@ -31,3 +31,29 @@ def test_hash_ignores_comment_edits_only():
     changed[k] = files[k].replace("constexpr int SPIN_LIMIT = 1 << 22;", "constexpr int SPIN_LIMIT = 1 << 21;", 1)
     assert changed[k] != files[k]
     assert bench.kernel_source_hash(changed.__getitem__) != base
+
+
+def _run_bench(args, env_extra=None):
+    import json
+    import subprocess
+    env = dict(os.environ, **(env_extra or {}))
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), *args], capture_output=True, text=True,
+                       env=env, cwd=ROOT, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    return [json.loads(ln) for ln in r.stdout.splitlines() if ln.startswith("{")]
+
+
+def test_reference_arm_line():
+    # the reference arm is the oracle on the host cores: one JSON line with
+    # the contract's keys, no GPU needed; ranks other than 0 print nothing
+    lines = _run_bench(["--impl", "reference", "--events", "300000", "--steps", "1", "--warmup", "1"])
+    assert len(lines) == 1
+    d = lines[0]
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+    assert _run_bench(["--impl", "reference", "--events", "300000", "--steps", "1", "--warmup", "1"],
+                      {"RANK": "1"}) == []
