@@ -173,3 +173,24 @@ def test_noalloc_scratch_covers_a_million_events_in_every_key_format(rv):
     for text, codes, bits in cases:
         f = rv.Formula(text, codes, key_bits=bits)
         assert rv.workspace_size(f, 1_000_000) <= 64 << 20, (text, bits)
+
+
+def test_batch_arguments_are_checked_before_any_device_work(rv):
+    # rv_batch_create validates its formulas and offsets on the host and
+    # returns an error before it allocates or copies anything
+    import numpy as np
+    c2, c3 = ["p0", "p1"], ["p0", "p1", "p2"]
+    f2 = rv.Formula("A x: p(x) => G p0", c2)
+    f3 = rv.Formula("A x: p(x) => G p0", c3)
+    nested = rv.Formula("A_{>=0.90} u: user(u) => E_{<=3} f: file(u,f) => open && !F close",
+                        ["user", "file", "open", "close"], key_bits=64)
+    off = np.array([0, 10, 20], dtype=np.uint64)
+    cases = [([[f2, f3], [f2, f2]], off, rv.RV_EINVAL),                              # alphabets differ in a trace
+             ([[nested], [nested]], off, rv.RV_EUNSUPPORTED),                        # two quantifiers
+             ([[f2], [f2]], np.array([0, 20, 10], dtype=np.uint64), rv.RV_EINVAL),   # decreasing offsets
+             ([[f2], [f2]], np.array([5, 10, 20], dtype=np.uint64), rv.RV_EINVAL),   # offsets[0] != 0
+             ([[f2] * 33, [f2] * 33], off, rv.RV_EINVAL)]                            # more than 32 formulas
+    for forms, o, want in cases:
+        with pytest.raises(rv.RVError) as e:
+            rv.Batch(forms, o)
+        assert e.value.status == want, (e.value, want)
